@@ -1,0 +1,152 @@
+/*
+ * pp.h -- C ABI of libpp: noisy-inverse Pauli propagation on one B300 GPU.
+ *
+ * The library propagates an observable O, held as a sum of bit-packed Pauli
+ * strings, backwards (Heisenberg picture) through a circuit of Pauli rotations
+ * U = exp(-i theta R / 2) and sparse Pauli-Lindblad noise maps, giving the
+ * noise-canceling observable O~ and its value <0..0|O~|0..0>.
+ *
+ *   gate rule (Sec. I, Eq. evolve_gate; Heisenberg form in App. G):
+ *       U^dag P U = cos(theta) P + i sin(theta) R P      if P, R anticommute
+ *                 = P                                   otherwise
+ *   inverse-noise rule (Sec. I, Eq. evolve_noise, with q = (1 - e^{2 lambda})/2,
+ *   so 1 - 2q = e^{+2 lambda}; App. G, Eq. evolve_noise_fid):
+ *       Lambda^{-1}(P) = exp(+2 * sum_{k: {P,E_k} = 0} lambda_k) P
+ *   truncation (Sec. I.A): after every gate and every noise map, a string is
+ *       dropped when its coefficient is 0, |c| < eps, or its Pauli weight
+ *       exceeds w_max.
+ *
+ * Conventions
+ *   Qubits: n_qubits <= 128.  W = ceil(n_qubits / 64) uint64 words per mask.
+ *   A Pauli string is (x[W], z[W]): bit q of word q/64 is qubit q; letter
+ *   (x,z) = (0,0) I, (1,0) X, (1,1) Y, (0,1) Z.  Strings are Hermitian and every
+ *   sign lives in the real coefficient.  Arrays of strings are row-major
+ *   [count][W].
+ *   Time order: layer 0 is applied to the state first.  A layer is a set of
+ *   pairwise-commuting rotations; the backward pass applies a layer's gates in
+ *   the order they are listed (the order only matters through truncation).
+ *   A noise map attached to layer l acts after layer l's gates in time, so the
+ *   backward pass applies it before them.
+ *
+ * Ownership and errors
+ *   Every pointer argument is a HOST pointer unless its name ends in _dev.  The
+ *   library copies all inputs; the caller keeps ownership of its buffers.  The
+ *   handle owns its device memory, obtained through pp_options.alloc (or
+ *   cudaMalloc when NULL) and released by pp_destroy.  Every call returns a
+ *   pp_status; PP_OK is 0.  On any other status the handle stays valid and
+ *   pp_last_error() describes the failure; results of a failed pp_propagate are
+ *   discarded.  Calls on one handle must not overlap; distinct handles are
+ *   independent.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pp_handle pp_handle;
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_ARG = 1,       /* invalid argument (sizes, layer indices, non-commuting layer) */
+    PP_ERR_STATE = 2,     /* call out of order (e.g. pp_expect before pp_propagate)       */
+    PP_ERR_NOMEM = 3,     /* device allocation failed                                      */
+    PP_ERR_CAPACITY = 4,  /* live terms exceeded the handle's capacity                     */
+    PP_ERR_CUDA = 5,      /* a CUDA runtime call failed                                    */
+    PP_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up                            */
+} pp_status;
+
+enum { PP_PRECISION_FP64 = 64, PP_PRECISION_FP32 = 32 };
+enum { PP_NOISE_INVERSE = 0, PP_NOISE_FORWARD = 1 };
+
+typedef struct {
+    int precision;                 /* PP_PRECISION_FP64 (default) or PP_PRECISION_FP32:
+                                      storage and branching type of coefficients; noise
+                                      exponents and the final sum are always exact or FP64 */
+    size_t max_terms;              /* live-term capacity per buffer; 0 = derive from free memory */
+    void* (*alloc)(size_t bytes, void* ctx);   /* device allocator; NULL = cudaMalloc */
+    void (*free)(void* ptr, void* ctx);        /* matching release; NULL = cudaFree   */
+    void* alloc_ctx;
+    void* cuda_stream;             /* cudaStream_t to run on; NULL = the legacy default stream */
+} pp_options;
+
+/* Fills *opt with defaults (FP64, automatic capacity, cudaMalloc, default stream). */
+void pp_default_options(pp_options* opt);
+
+/* Creates a handle for n_qubits (1..128).  opt may be NULL (defaults).
+ * Errors: PP_ERR_ARG (n_qubits out of range, out NULL), PP_ERR_CUDA. */
+pp_status pp_create(const pp_options* opt, int n_qubits, pp_handle** out);
+
+/* Releases the handle and all its device memory.  NULL is a no-op. */
+pp_status pp_destroy(pp_handle* h);
+
+/* Loads the circuit (Sec. I: time-ordered Pauli rotations U_t = exp(-i R_t theta_t / 2)).
+ *   rx, rz     [n_gates][W] generator R of each gate
+ *   theta      [n_gates]    rotation angle
+ *   layer_of   [n_gates]    layer index, non-decreasing, >= 0; n_layers = last + 1
+ *                           (layers without gates are allowed and may carry noise)
+ *   n_layers   number of layers (>= 1 + max(layer_of)); lets trailing layers be empty
+ * Gates of one layer must pairwise commute (else PP_ERR_ARG).  Clears any
+ * previously loaded noise.  cos/sin of each angle are taken on the host; values
+ * with magnitude below 1e-15 snap to exactly 0 (and the other to +-1). */
+pp_status pp_load_circuit(pp_handle* h, size_t n_gates, const uint64_t* rx, const uint64_t* rz,
+                          const double* theta, const int32_t* layer_of, int n_layers);
+
+/* Attaches a sparse Pauli-Lindblad noise map after `layer` in time (Sec. I,
+ * Lambda_t = composition of (1-p) . + p E . E with p = (1 - e^{-2 lambda})/2).
+ *   ex, ez   [n_gen][W] generators E_k;  lambda [n_gen] rates, >= 0
+ *   mode     PP_NOISE_INVERSE: coefficients scale by exp(+2 sum lambda) (antinoise);
+ *            PP_NOISE_FORWARD: by exp(-2 sum lambda) (the physical channel)
+ * Generators of weight 1 and 2 are evaluated from per-site and per-pair tables;
+ * heavier ones from a generic list.  Replaces a map previously attached to the layer. */
+pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* ex,
+                        const uint64_t* ez, const double* lambda, int mode);
+
+/* Propagates O = sum_t oc[t] P(ox[t], oz[t]) backwards through every layer.
+ *   ox, oz [n_terms][W], oc [n_terms]; duplicate strings are summed.
+ *   eps    coefficient threshold (>= 0; 0 keeps every nonzero term)
+ *   w_max  Pauli-weight cap (< 0: none)
+ * Synchronises the handle's stream.  Errors: PP_ERR_STATE (no circuit),
+ * PP_ERR_ARG, PP_ERR_NOMEM, PP_ERR_CAPACITY (more live terms than the capacity;
+ * raise pp_options.max_terms), PP_ERR_CUDA. */
+pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const uint64_t* oz,
+                       const double* oc, double eps, int w_max);
+
+/* <0..0|O~|0..0> = sum of c over strings with no X or Y letter, of the last
+ * successful pp_propagate.  Accumulated exactly in 128-bit fixed point (terms
+ * below 2^-80 in magnitude are cut), so the value does not depend on term order.
+ * Synchronises.  Errors: PP_ERR_STATE. */
+pp_status pp_expect(pp_handle* h, double* value);
+
+/* Copies O~ to caller-owned host buffers, sorted by (x, then z) as unsigned
+ * integers (word W-1 most significant).  x, z: [cap][W], c: [cap] (FP64 in both
+ * precisions).  *n_out = number of terms; PP_ERR_CAPACITY if cap < *n_out (nothing
+ * copied).  Any of x, z, c may be NULL to query *n_out only. */
+pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, double* c,
+                          size_t* n_out);
+
+typedef struct {
+    size_t n_terms;          /* live terms of O~                                        */
+    size_t peak_terms;       /* largest live-term count after any sub-layer             */
+    double updates;          /* sum over gates of the live terms entering the gate
+                                (canonical gate-by-gate count)                           */
+    int n_sublayers;         /* fused sub-layers executed                               */
+    int kernel_launches;     /* kernels this library launched in the last propagation  */
+    int fallback_buckets;    /* buckets processed by the global-memory path            */
+    double seconds;          /* wall time of the last pp_propagate (host clock)        */
+} pp_stats;
+
+pp_status pp_get_stats(const pp_handle* h, pp_stats* out);
+
+/* Description of the last failure on this handle ("" if none).  Valid until the next call. */
+const char* pp_last_error(const pp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H */

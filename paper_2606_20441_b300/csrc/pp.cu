@@ -1,0 +1,862 @@
+// libpp host side: the C ABI of include/pp.h, circuit planning into fused
+// sub-layers, noise tables, the per-sub-layer launch sequence, capacity
+// management, expectation and export.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "pp.h"
+#include "pp_kernels.cuh"
+
+using namespace pp;
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kTileCap1 = 2048;   // shared-memory tile entries, W = 1
+constexpr int kTileCap2 = 1024;   // W = 2
+constexpr int kFallbackCTAs = 16;
+constexpr int kFallbackCap = 1 << 20;
+
+struct NoiseHost {
+    int mode = 0;
+    std::vector<int64_t> t1;          // [n][4]
+    std::vector<int32_t> pair_off, pair_other, pair_id;
+    std::vector<int64_t> t2;          // [P][16]
+    std::vector<uint64_t> gx, gz;
+    std::vector<int64_t> glam;
+    // device copies
+    int64_t* d_t1 = nullptr;
+    int32_t* d_pair_off = nullptr;
+    int32_t* d_pair_other = nullptr;
+    int32_t* d_pair_id = nullptr;
+    int64_t* d_t2 = nullptr;
+    uint64_t* d_gx = nullptr;
+    uint64_t* d_gz = nullptr;
+    int64_t* d_glam = nullptr;
+};
+
+struct Arena {
+    uint64_t* x = nullptr;
+    uint64_t* z = nullptr;
+    void* c = nullptr;
+};
+
+}  // namespace
+
+struct pp_handle {
+    pp_options opt;
+    int n = 0, W = 1;
+    cudaStream_t st = nullptr;
+    std::string err;
+    int sm_count = 0;
+
+    // circuit
+    bool have_circuit = false;
+    int n_layers = 0;
+    std::vector<uint64_t> gx, gz;
+    std::vector<double> theta;
+    std::vector<int32_t> layer_of;
+    std::map<int, NoiseHost> noise;
+    std::vector<SubLayerDesc> subs;
+    std::vector<int> sub_kind;     // growth-estimate class of each sub-layer
+    SubLayerDesc* d_subs = nullptr;
+    bool subs_dirty = true;
+
+    // memory
+    size_t cap = 0;                // terms per arena
+    Arena arena[2];
+    uint32_t* fill[2] = {nullptr, nullptr};
+    uint32_t fill_cap = 0;
+    unsigned long long* counters = nullptr;
+    long long* delta = nullptr;
+    uint32_t* deferred = nullptr;
+    unsigned char* fb_scratch = nullptr;
+    size_t fb_slice = 0;
+    uint64_t* stage = nullptr;     // input staging
+    size_t stage_cap = 0;
+    __int128* partial = nullptr;
+    std::vector<void*> owned;
+
+    // result
+    bool have_result = false;
+    int res_side = 0;
+    size_t n_res = 0;
+    pp_stats stats{};
+};
+
+namespace {
+
+pp_status fail(pp_handle* h, pp_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, PP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+void* dev_alloc(pp_handle* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (h->opt.alloc) {
+        p = h->opt.alloc(bytes, h->opt.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) h->owned.push_back(p);
+    return p;
+}
+
+void dev_free(pp_handle* h, void* p) {
+    if (!p) return;
+    auto it = std::find(h->owned.begin(), h->owned.end(), p);
+    if (it != h->owned.end()) h->owned.erase(it);
+    if (h->opt.free) h->opt.free(p, h->opt.alloc_ctx);
+    else cudaFree(p);
+}
+
+template <typename P>
+P* alloc_copy(pp_handle* h, const std::vector<typename std::remove_const<P>::type>& v) {
+    size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(P);
+    P* d = static_cast<P*>(dev_alloc(h, bytes));
+    if (d && !v.empty()) cudaMemcpyAsync((void*)d, v.data(), v.size() * sizeof(P), cudaMemcpyHostToDevice, h->st);
+    return d;
+}
+
+inline int popc_words(const uint64_t* v, int W) {
+    int s = 0;
+    for (int w = 0; w < W; ++w) s += __builtin_popcountll(v[w]);
+    return s;
+}
+
+inline int bit(const uint64_t* v, int q) { return (int)((v[q >> 6] >> (q & 63)) & 1ull); }
+
+void trig(double theta, double* c, double* s) {
+    *c = std::cos(theta);
+    *s = std::sin(theta);
+    if (std::fabs(*c) < 1e-15) { *c = 0.0; *s = (*s > 0) ? 1.0 : -1.0; }
+    if (std::fabs(*s) < 1e-15) { *s = 0.0; *c = (*c > 0) ? 1.0 : -1.0; }
+}
+
+// Gate signature for grouping into sub-layers.
+struct GateSig {
+    int cls;      // CLS_LOCAL1 / CLS_LOCAL2 / CLS_GENERIC
+    int ax, az, bx, bz, shift;
+    int slot;     // first site
+    bool same(const GateSig& o) const {
+        return cls == o.cls && ax == o.ax && az == o.az && bx == o.bx && bz == o.bz && shift == o.shift;
+    }
+};
+
+GateSig classify(const uint64_t* rx, const uint64_t* rz, int n, int W) {
+    GateSig g{CLS_GENERIC, 0, 0, 0, 0, 0, -1};
+    uint64_t sup[MAXW] = {0, 0};
+    for (int w = 0; w < W; ++w) sup[w] = rx[w] | rz[w];
+    int wt = popc_words(sup, W);
+    std::vector<int> sites;
+    for (int q = 0; q < n; ++q)
+        if (bit(sup, q)) sites.push_back(q);
+    if (wt == 1) {
+        g.cls = CLS_LOCAL1;
+        g.slot = sites[0];
+        g.ax = bit(rx, sites[0]);
+        g.az = bit(rz, sites[0]);
+    } else if (wt == 2) {
+        g.cls = CLS_LOCAL2;
+        g.slot = sites[0];
+        g.ax = bit(rx, sites[0]);
+        g.az = bit(rz, sites[0]);
+        g.bx = bit(rx, sites[1]);
+        g.bz = bit(rz, sites[1]);
+        g.shift = sites[1] - sites[0];
+    }
+    return g;
+}
+
+int sig_kind(const SubLayerDesc& d) {
+    if (d.cls == CLS_LOCAL1) return 1 + 4 * (d.ax + 2 * d.az);
+    if (d.cls == CLS_LOCAL2) return 2 + 4 * (d.ax + 2 * d.az + 4 * (d.bx + 2 * d.bz) + 16 * d.shift);
+    return d.cls;
+}
+
+// Splits a layer's gates (listed order) into fused sub-layers.
+void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int layer) {
+    const int W = h->W, n = h->n;
+    std::vector<SubLayerDesc> out;
+    SubLayerDesc cur;
+    bool open = false;
+    GateSig cur_sig{};
+    int last_slot = -1;
+    std::vector<bool> used(MAX_SITES, false);
+    auto close = [&]() {
+        if (open) out.push_back(cur);
+        open = false;
+    };
+    auto start = [&](const GateSig& s) {
+        std::memset(&cur, 0, sizeof(cur));
+        cur.cls = s.cls;
+        cur.ax = s.ax; cur.az = s.az; cur.bx = s.bx; cur.bz = s.bz; cur.shift = s.shift;
+        cur.noise = -1;
+        cur.nseg = 0;
+        open = true;
+        cur_sig = s;
+        last_slot = -1;
+        std::fill(used.begin(), used.end(), false);
+    };
+    for (int g : gates) {
+        const uint64_t* rx = &h->gx[(size_t)g * W];
+        const uint64_t* rz = &h->gz[(size_t)g * W];
+        GateSig s = classify(rx, rz, n, W);
+        double cs, sn;
+        trig(h->theta[g], &cs, &sn);
+        if (s.cls == CLS_GENERIC) {
+            if (!(open && cur.cls == CLS_GENERIC && cur.n_gates < MAX_GEN)) {
+                close();
+                start(s);
+            }
+            int j = cur.n_gates++;
+            for (int w = 0; w < W; ++w) {
+                cur.gx[j][w] = rx[w];
+                cur.gz[j][w] = rz[w];
+            }
+            cur.cs[j] = cs;
+            cur.sn[j] = sn;
+            cur.order[j] = (int16_t)j;
+            continue;
+        }
+        bool fits = open && cur.cls != CLS_GENERIC && cur_sig.same(s) && !used[s.slot] &&
+                    (s.slot > last_slot || cur.nseg < MAX_SEG);
+        if (!fits) {
+            close();
+            start(s);
+        }
+        if (s.slot <= last_slot || cur.nseg == 0) cur.nseg++;
+        int sg = cur.nseg - 1;
+        cur.seg[sg][s.slot >> 6] |= 1ull << (s.slot & 63);
+        cur.all[s.slot >> 6] |= 1ull << (s.slot & 63);
+        cur.cs[s.slot] = cs;
+        cur.sn[s.slot] = sn;
+        cur.order[s.slot] = (int16_t)cur.n_gates;
+        cur.n_gates++;
+        used[s.slot] = true;
+        last_slot = s.slot;
+    }
+    close();
+    if (out.empty() && noise_idx >= 0) {
+        SubLayerDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.cls = CLS_NONE;
+        d.noise = -1;
+        out.push_back(d);
+    }
+    if (!out.empty()) out[0].noise = noise_idx;
+    for (auto& d : out) {
+        h->subs.push_back(d);
+        h->sub_kind.push_back(sig_kind(d));
+    }
+    (void)layer;
+}
+
+pp_status build_plan(pp_handle* h) {
+    h->subs.clear();
+    h->sub_kind.clear();
+    std::vector<std::vector<int>> by_layer(h->n_layers);
+    for (size_t g = 0; g < h->theta.size(); ++g) by_layer[h->layer_of[g]].push_back((int)g);
+    for (int l = h->n_layers - 1; l >= 0; --l) {
+        int nz = h->noise.count(l) ? l : -1;
+        plan_layer(h, by_layer[l], nz, l);
+    }
+    if (h->subs.empty()) {
+        SubLayerDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.cls = CLS_NONE;
+        d.noise = -1;
+        h->subs.push_back(d);
+        h->sub_kind.push_back(0);
+    }
+    h->subs.front().first = 1;
+    h->subs.back().final_ = 1;
+    if (h->d_subs) dev_free(h, h->d_subs);
+    h->d_subs = static_cast<SubLayerDesc*>(dev_alloc(h, sizeof(SubLayerDesc) * h->subs.size()));
+    if (!h->d_subs) return fail(h, PP_ERR_NOMEM, "descriptor allocation failed");
+    CK(cudaMemcpyAsync(h->d_subs, h->subs.data(), sizeof(SubLayerDesc) * h->subs.size(),
+                       cudaMemcpyHostToDevice, h->st));
+    h->subs_dirty = false;
+    return PP_OK;
+}
+
+size_t term_bytes(const pp_handle* h) {
+    return 2 * (size_t)h->W * 8 + (h->opt.precision == PP_PRECISION_FP32 ? 4 : 8);
+}
+
+int tile_cap(const pp_handle* h) { return h->W == 1 ? kTileCap1 : kTileCap2; }
+
+size_t tile_smem(const pp_handle* h) {
+    size_t per = h->opt.precision == PP_PRECISION_FP32
+                     ? (h->W == 1 ? tile_bytes_per_entry<1, float>() : tile_bytes_per_entry<2, float>())
+                     : (h->W == 1 ? tile_bytes_per_entry<1, double>() : tile_bytes_per_entry<2, double>());
+    return per * (size_t)tile_cap(h);
+}
+
+pp_status ensure_memory(pp_handle* h) {
+    if (h->arena[0].x) return PP_OK;
+    size_t tb = term_bytes(h);
+    size_t cap = h->opt.max_terms;
+    if (cap == 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        // two arenas take at most 60% of free memory
+        cap = (size_t)(0.30 * (double)fr) / tb;
+    }
+    cap = std::max<size_t>(cap, 4096);
+    h->cap = cap;
+    for (int s = 0; s < 2; ++s) {
+        h->arena[s].x = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
+        h->arena[s].z = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
+        h->arena[s].c = dev_alloc(h, cap * (h->opt.precision == PP_PRECISION_FP32 ? 4 : 8));
+        if (!h->arena[s].x || !h->arena[s].z || !h->arena[s].c)
+            return fail(h, PP_ERR_NOMEM, "term arena allocation (%zu terms) failed", cap);
+    }
+    h->fill_cap = (uint32_t)std::min<size_t>(std::max<size_t>(cap / 64, 1024), 1u << 28);
+    for (int s = 0; s < 2; ++s) {
+        h->fill[s] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
+        if (!h->fill[s]) return fail(h, PP_ERR_NOMEM, "bucket counters allocation failed");
+    }
+    h->counters = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * CTR_COUNT));
+    h->delta = static_cast<long long*>(dev_alloc(h, sizeof(long long) * MAX_SITES));
+    h->deferred = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
+    h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * 4096));
+    size_t per = h->opt.precision == PP_PRECISION_FP32
+                     ? (h->W == 1 ? tile_bytes_per_entry<1, float>() : tile_bytes_per_entry<2, float>())
+                     : (h->W == 1 ? tile_bytes_per_entry<1, double>() : tile_bytes_per_entry<2, double>());
+    h->fb_slice = (per * kFallbackCap + 255) & ~(size_t)255;
+    h->fb_scratch = static_cast<unsigned char*>(dev_alloc(h, h->fb_slice * kFallbackCTAs));
+    if (!h->counters || !h->delta || !h->deferred || !h->partial || !h->fb_scratch)
+        return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
+    return PP_OK;
+}
+
+uint32_t pow2_at_least(double v, uint32_t cap) {
+    uint32_t b = 1;
+    while ((double)b < v && b < cap) b <<= 1;
+    return b;
+}
+
+template <int W, typename T>
+cudaError_t launch_process(pp_handle* h, const StepParams& p, bool fallback, uint32_t n_def, int* launches) {
+    if (!fallback) {
+        int cap = W == 1 ? kTileCap1 : kTileCap2;
+        size_t smem = tile_bytes_per_entry<W, T>() * (size_t)cap;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_process<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_set = true;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T>, kThreads, smem);
+        per_sm = std::max(per_sm, 1);
+        uint32_t grid = std::min<uint32_t>(p.sB, (uint32_t)(per_sm * h->sm_count));
+        k_process<W, T><<<grid, kThreads, smem, h->st>>>(p, cap);
+    } else {
+        uint32_t grid = std::min<uint32_t>(n_def, (uint32_t)kFallbackCTAs);
+        k_process_global<W, T><<<grid, kThreads, 0, h->st>>>(p, h->fb_scratch, h->fb_slice, kFallbackCap, n_def);
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_process(pp_handle* h, const StepParams& p, bool fb, uint32_t n_def, int* launches) {
+    bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    if (h->W == 1) return f32 ? launch_process<1, float>(h, p, fb, n_def, launches)
+                              : launch_process<1, double>(h, p, fb, n_def, launches);
+    return f32 ? launch_process<2, float>(h, p, fb, n_def, launches)
+               : launch_process<2, double>(h, p, fb, n_def, launches);
+}
+
+cudaError_t dispatch_scatter(pp_handle* h, const uint64_t* ox, const uint64_t* oz, const double* oc,
+                             size_t n, const StepParams& p, int* launches) {
+    bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+    grid = std::max(grid, 1);
+    if (h->W == 1) {
+        if (f32) k_scatter_input<1, float><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
+        else k_scatter_input<1, double><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
+    } else {
+        if (f32) k_scatter_input<2, float><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
+        else k_scatter_input<2, double><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+NoiseDesc noise_desc(const NoiseHost& nh) {
+    NoiseDesc d;
+    d.mode = nh.mode;
+    d.n_generic = (int)nh.glam.size();
+    d.t1 = nh.d_t1;
+    d.pair_off = nh.d_pair_off;
+    d.pair_other = nh.d_pair_other;
+    d.pair_id = nh.d_pair_id;
+    d.t2 = nh.d_t2;
+    d.gen_x = nh.d_gx;
+    d.gen_z = nh.d_gz;
+    d.gen_lam = nh.d_glam;
+    return d;
+}
+
+float eps_float_ceil(double eps) {
+    float f = (float)eps;
+    if ((double)f < eps) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pp_default_options(pp_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = PP_PRECISION_FP64;
+}
+
+pp_status pp_create(const pp_options* opt, int n_qubits, pp_handle** out) {
+    if (!out) return PP_ERR_ARG;
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > MAXW * 64) return PP_ERR_ARG;
+    pp_handle* h = new pp_handle();
+    if (opt) h->opt = *opt;
+    else pp_default_options(&h->opt);
+    if (h->opt.precision != PP_PRECISION_FP32) h->opt.precision = PP_PRECISION_FP64;
+    h->n = n_qubits;
+    h->W = (n_qubits + 63) / 64;
+    h->st = static_cast<cudaStream_t>(h->opt.cuda_stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return PP_ERR_CUDA;
+    }
+    *out = h;
+    return PP_OK;
+}
+
+pp_status pp_destroy(pp_handle* h) {
+    if (!h) return PP_OK;
+    cudaStreamSynchronize(h->st);
+    std::vector<void*> all = h->owned;
+    for (void* p : all) dev_free(h, p);
+    delete h;
+    return PP_OK;
+}
+
+const char* pp_last_error(const pp_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+pp_status pp_load_circuit(pp_handle* h, size_t n_gates, const uint64_t* rx, const uint64_t* rz,
+                          const double* theta, const int32_t* layer_of, int n_layers) {
+    if (!h) return PP_ERR_ARG;
+    h->err.clear();
+    if (n_gates && (!rx || !rz || !theta || !layer_of)) return fail(h, PP_ERR_ARG, "null gate arrays");
+    if (n_layers < 1) return fail(h, PP_ERR_ARG, "n_layers must be >= 1");
+    const int W = h->W, n = h->n;
+    for (size_t g = 0; g < n_gates; ++g) {
+        if (layer_of[g] < 0 || layer_of[g] >= n_layers)
+            return fail(h, PP_ERR_ARG, "gate %zu: layer %d out of [0,%d)", g, layer_of[g], n_layers);
+        if (!std::isfinite(theta[g])) return fail(h, PP_ERR_ARG, "gate %zu: angle not finite", g);
+        int wt = 0;
+        for (int w = 0; w < W; ++w) {
+            uint64_t sup = rx[g * W + w] | rz[g * W + w];
+            if (w == W - 1 && (n % 64) && (sup >> (n % 64)))
+                return fail(h, PP_ERR_ARG, "gate %zu acts beyond qubit %d", g, n - 1);
+            wt += __builtin_popcountll(sup);
+        }
+        if (wt == 0) return fail(h, PP_ERR_ARG, "gate %zu: identity generator", g);
+    }
+    // gates of one layer must pairwise commute
+    std::vector<std::vector<size_t>> by_layer(n_layers);
+    for (size_t g = 0; g < n_gates; ++g) by_layer[layer_of[g]].push_back(g);
+    for (int l = 0; l < n_layers; ++l) {
+        const auto& gl = by_layer[l];
+        for (size_t i = 0; i < gl.size(); ++i)
+            for (size_t j = i + 1; j < gl.size(); ++j) {
+                int s = 0;
+                for (int w = 0; w < W; ++w)
+                    s += __builtin_popcountll((rx[gl[i] * W + w] & rz[gl[j] * W + w]) ^
+                                              (rz[gl[i] * W + w] & rx[gl[j] * W + w]));
+                if (s & 1)
+                    return fail(h, PP_ERR_ARG, "gates %zu and %zu of layer %d do not commute", gl[i], gl[j], l);
+            }
+    }
+    h->gx.assign(rx, rx + n_gates * W);
+    h->gz.assign(rz, rz + n_gates * W);
+    h->theta.assign(theta, theta + n_gates);
+    h->layer_of.assign(layer_of, layer_of + n_gates);
+    h->n_layers = n_layers;
+    for (auto& kv : h->noise) {
+        NoiseHost& nh = kv.second;
+        for (void* p : {(void*)nh.d_t1, (void*)nh.d_pair_off, (void*)nh.d_pair_other, (void*)nh.d_pair_id,
+                        (void*)nh.d_t2, (void*)nh.d_gx, (void*)nh.d_gz, (void*)nh.d_glam})
+            dev_free(h, p);
+    }
+    h->noise.clear();
+    h->have_circuit = true;
+    h->have_result = false;
+    h->subs_dirty = true;
+    return PP_OK;
+}
+
+pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* ex, const uint64_t* ez,
+                        const double* lambda, int mode) {
+    if (!h) return PP_ERR_ARG;
+    h->err.clear();
+    if (!h->have_circuit) return fail(h, PP_ERR_STATE, "load the circuit before its noise");
+    if (layer < 0 || layer >= h->n_layers) return fail(h, PP_ERR_ARG, "layer %d out of range", layer);
+    if (mode != PP_NOISE_INVERSE && mode != PP_NOISE_FORWARD) return fail(h, PP_ERR_ARG, "bad noise mode");
+    if (n_gen && (!ex || !ez || !lambda)) return fail(h, PP_ERR_ARG, "null generator arrays");
+    const int W = h->W, n = h->n;
+    NoiseHost nh;
+    nh.mode = mode;
+    nh.t1.assign((size_t)n * 4, 0);
+    std::map<std::pair<int, int>, int> pid;
+    std::vector<std::pair<int, int>> pairs;
+    double total = 0.0;
+    // anticommutation of single-qubit letters (code x + 2z) by the symplectic form
+    auto anti1 = [](int l, int e) { return ((l & 1) & (e >> 1)) ^ ((l >> 1) & (e & 1)); };
+    for (size_t k = 0; k < n_gen; ++k) {
+        const uint64_t* x = ex + k * W;
+        const uint64_t* z = ez + k * W;
+        if (!(lambda[k] >= 0.0) || !std::isfinite(lambda[k]))
+            return fail(h, PP_ERR_ARG, "generator %zu: rate must be finite and >= 0", k);
+        total += lambda[k];
+        int64_t lf = (int64_t)std::llround(std::ldexp(lambda[k], FIX_SHIFT));
+        std::vector<int> sites;
+        for (int q = 0; q < n; ++q)
+            if (bit(x, q) | bit(z, q)) sites.push_back(q);
+        for (int w = 0; w < W; ++w) {
+            uint64_t sup = x[w] | z[w];
+            if (w == W - 1 && (n % 64) && (sup >> (n % 64)))
+                return fail(h, PP_ERR_ARG, "generator %zu acts beyond qubit %d", k, n - 1);
+        }
+        if (sites.size() == 1) {
+            int q = sites[0];
+            int e = bit(x, q) + 2 * bit(z, q);
+            for (int l = 1; l < 4; ++l)
+                if (anti1(l, e)) nh.t1[4 * q + l] += lf;
+        } else if (sites.size() == 2) {
+            int a = sites[0], b = sites[1];
+            auto key = std::make_pair(a, b);
+            int id;
+            auto it = pid.find(key);
+            if (it == pid.end()) {
+                id = (int)pairs.size();
+                pid[key] = id;
+                pairs.push_back(key);
+                nh.t2.resize(nh.t2.size() + 16, 0);
+            } else {
+                id = it->second;
+            }
+            int ea = bit(x, a) + 2 * bit(z, a), eb = bit(x, b) + 2 * bit(z, b);
+            for (int la = 0; la < 4; ++la)
+                for (int lb = 0; lb < 4; ++lb)
+                    if (anti1(la, ea) ^ anti1(lb, eb)) nh.t2[16 * id + la + 4 * lb] += lf;
+        } else if (sites.size() > 2) {
+            nh.gx.insert(nh.gx.end(), x, x + W);
+            nh.gz.insert(nh.gz.end(), z, z + W);
+            nh.glam.push_back(lf);
+        }
+    }
+    if (total >= 60.0) return fail(h, PP_ERR_ARG, "sum of rates %.3g too large (must be < 60)", total);
+    nh.pair_off.assign(n + 1, 0);
+    for (auto& pr : pairs) {
+        nh.pair_off[pr.first + 1]++;
+        nh.pair_off[pr.second + 1]++;
+    }
+    for (int q = 0; q < n; ++q) nh.pair_off[q + 1] += nh.pair_off[q];
+    nh.pair_other.assign(2 * pairs.size(), 0);
+    nh.pair_id.assign(2 * pairs.size(), 0);
+    std::vector<int> pos(nh.pair_off.begin(), nh.pair_off.end() - 1);
+    for (size_t i = 0; i < pairs.size(); ++i) {
+        int a = pairs[i].first, b = pairs[i].second;
+        nh.pair_other[pos[a]] = b;
+        nh.pair_id[pos[a]++] = (int)i;
+        nh.pair_other[pos[b]] = a;
+        nh.pair_id[pos[b]++] = (int)i;
+    }
+    auto old = h->noise.find(layer);
+    if (old != h->noise.end()) {
+        NoiseHost& o = old->second;
+        for (void* p : {(void*)o.d_t1, (void*)o.d_pair_off, (void*)o.d_pair_other, (void*)o.d_pair_id,
+                        (void*)o.d_t2, (void*)o.d_gx, (void*)o.d_gz, (void*)o.d_glam})
+            dev_free(h, p);
+        h->noise.erase(old);
+    }
+    nh.d_t1 = alloc_copy<int64_t>(h, nh.t1);
+    nh.d_pair_off = alloc_copy<int32_t>(h, nh.pair_off);
+    nh.d_pair_other = alloc_copy<int32_t>(h, nh.pair_other);
+    nh.d_pair_id = alloc_copy<int32_t>(h, nh.pair_id);
+    nh.d_t2 = alloc_copy<int64_t>(h, nh.t2);
+    nh.d_gx = alloc_copy<uint64_t>(h, nh.gx);
+    nh.d_gz = alloc_copy<uint64_t>(h, nh.gz);
+    nh.d_glam = alloc_copy<int64_t>(h, nh.glam);
+    if (!nh.d_t1 || !nh.d_pair_off || !nh.d_pair_other || !nh.d_pair_id || !nh.d_t2 || !nh.d_gx ||
+        !nh.d_gz || !nh.d_glam)
+        return fail(h, PP_ERR_NOMEM, "noise table allocation failed");
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, PP_ERR_CUDA, "noise upload failed");
+    h->noise[layer] = std::move(nh);
+    h->have_result = false;
+    h->subs_dirty = true;
+    return PP_OK;
+}
+
+pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const uint64_t* oz,
+                       const double* oc, double eps, int w_max) {
+    if (!h) return PP_ERR_ARG;
+    h->err.clear();
+    auto t0 = std::chrono::steady_clock::now();
+    if (!h->have_circuit) return fail(h, PP_ERR_STATE, "no circuit loaded");
+    if (n_terms && (!ox || !oz || !oc)) return fail(h, PP_ERR_ARG, "null observable arrays");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(h, PP_ERR_ARG, "eps must be finite and >= 0");
+    h->have_result = false;
+    pp_status st;
+    if (h->subs_dirty && (st = build_plan(h)) != PP_OK) return st;
+    if ((st = ensure_memory(h)) != PP_OK) return st;
+    const int W = h->W;
+    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    int launches = 0;
+    pp_stats stats{};
+
+    // stage the observable
+    size_t need = std::max<size_t>(n_terms, 1) * (2 * W + 1);
+    if (need > h->stage_cap) {
+        if (h->stage) dev_free(h, h->stage);
+        h->stage = static_cast<uint64_t*>(dev_alloc(h, need * 8));
+        if (!h->stage) return fail(h, PP_ERR_NOMEM, "staging allocation failed");
+        h->stage_cap = need;
+    }
+    if (n_terms > h->cap) return fail(h, PP_ERR_CAPACITY, "observable larger than capacity");
+    uint64_t* sx = h->stage;
+    uint64_t* sz = h->stage + n_terms * W;
+    double* sc = reinterpret_cast<double*>(h->stage + 2 * n_terms * W);
+    if (n_terms) {
+        CK(cudaMemcpyAsync(sx, ox, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(sz, oz, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(sc, oc, n_terms * 8, cudaMemcpyHostToDevice, h->st));
+    }
+
+    const size_t tcap = (size_t)tile_cap(h);
+    const double target = (double)tcap / 6.0;    // expected input strings per bucket
+    std::map<int, double> growth;                // observed output/input per sub-layer kind
+    int side = 0;
+    uint32_t B = pow2_at_least((double)n_terms / target, h->fill_cap);
+    uint64_t C = h->cap / B;
+    CK(cudaMemsetAsync(h->fill[side], 0, sizeof(uint32_t) * B, h->st));
+    CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+
+    StepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.eps = eps;
+    p.eps_f = eps_float_ceil(eps);
+    p.w_max = w_max;
+    p.counters = h->counters;
+    p.delta = h->delta;
+    p.deferred = h->deferred;
+
+    // scatter input into the first sub-layer's buckets
+    p.sx = h->arena[side].x;
+    p.sz = h->arena[side].z;
+    p.sc = h->arena[side].c;
+    p.scap = h->cap;
+    p.sfill = h->fill[side];
+    p.sB = B;
+    p.sC = C;
+    p.desc = h->d_subs;
+    if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, p, &launches));
+    unsigned long long ctr[CTR_COUNT];
+    CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input scatter overflowed a bucket");
+    size_t N = n_terms;
+    size_t peak = N;
+    double updates = 0.0;
+
+    const int S = (int)h->subs.size();
+    for (int s = 0; s < S; ++s) {
+        const SubLayerDesc& d = h->subs[s];
+        const bool fin = d.final_ != 0;
+        int kind = h->sub_kind[s];
+        double g = growth.count(kind) ? growth[kind] : 3.0;
+        double est = std::max(64.0, (double)N * g * 1.3);
+        uint32_t nB = fin ? 1 : pow2_at_least(est / target, h->fill_cap);
+        int attempt = 0;
+        for (;;) {
+            uint64_t nC = fin ? h->cap : h->cap / nB;
+            if (!fin) CK(cudaMemsetAsync(h->fill[side ^ 1], 0, sizeof(uint32_t) * nB, h->st));
+            CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+            CK(cudaMemsetAsync(h->delta, 0, sizeof(long long) * MAX_SITES, h->st));
+            p.sx = h->arena[side].x;
+            p.sz = h->arena[side].z;
+            p.sc = h->arena[side].c;
+            p.scap = h->cap;
+            p.sfill = h->fill[side];
+            p.sB = B;
+            p.sC = C;
+            p.dx = h->arena[side ^ 1].x;
+            p.dz = h->arena[side ^ 1].z;
+            p.dc = h->arena[side ^ 1].c;
+            p.dcap = h->cap;
+            p.dfill = h->fill[side ^ 1];
+            p.dB = nB;
+            p.dC = nC;
+            p.desc = h->d_subs + s;
+            p.next = fin ? nullptr : h->d_subs + s + 1;
+            p.has_noise = d.noise >= 0;
+            if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
+            p.max_load = (uint32_t)(tcap / 2);
+            CK(dispatch_process(h, p, false, 0, &launches));
+            CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            if (ctr[CTR_DEFERRED]) {
+                uint32_t nd = (uint32_t)ctr[CTR_DEFERRED];
+                stats.fallback_buckets += (int)nd;
+                CK(dispatch_process(h, p, true, nd, &launches));
+                CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
+                CK(cudaStreamSynchronize(h->st));
+                if (ctr[CTR_ERR_FALLBACK])
+                    return fail(h, PP_ERR_CAPACITY,
+                                "sub-layer %d: a bucket exceeds the global-memory tile (%d entries)", s,
+                                kFallbackCap);
+            }
+            if (ctr[CTR_ERR_REGION] == 0) break;
+            if (fin || ctr[CTR_OUT] > h->cap || ++attempt > 4)
+                return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed capacity %zu", s,
+                            (unsigned long long)ctr[CTR_OUT], h->cap);
+            // a bucket region overflowed: fewer, larger regions and run the sub-layer again
+            nB = std::max<uint32_t>(1, nB / 4);
+        }
+        long long dl[MAX_SITES];
+        CK(cudaMemcpyAsync(dl, h->delta, sizeof(dl), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        // canonical gate-by-gate count: live terms entering each gate in listed order
+        double live = (double)ctr[CTR_PROLOGUE];
+        for (int j = 0; j < d.n_gates; ++j) {
+            updates += live;
+            live += (double)dl[j];
+        }
+        size_t Nout = (size_t)ctr[CTR_OUT];
+        if (N > 0) growth[kind] = std::max(0.05, (double)Nout / (double)N);
+        N = Nout;
+        peak = std::max(peak, N);
+        side ^= 1;
+        B = nB;
+        C = fin ? h->cap : h->cap / nB;
+        stats.n_sublayers++;
+    }
+    h->res_side = side;
+    h->n_res = N;
+    h->have_result = true;
+    stats.n_terms = N;
+    stats.peak_terms = peak;
+    stats.updates = updates;
+    stats.kernel_launches = launches;
+    stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    h->stats = stats;
+    (void)f32;
+    return PP_OK;
+}
+
+pp_status pp_expect(pp_handle* h, double* value) {
+    if (!h || !value) return PP_ERR_ARG;
+    h->err.clear();
+    if (!h->have_result) return fail(h, PP_ERR_STATE, "no propagation result");
+    const Arena& a = h->arena[h->res_side];
+    int grid = (int)std::min<size_t>(std::max<size_t>((h->n_res + 255) / 256, 1), 4096);
+    if (h->opt.precision == PP_PRECISION_FP32) {
+        if (h->W == 1) k_expect<1, float><<<grid, 256, 0, h->st>>>(a.x, (const float*)a.c, h->cap, h->n_res, h->partial);
+        else k_expect<2, float><<<grid, 256, 0, h->st>>>(a.x, (const float*)a.c, h->cap, h->n_res, h->partial);
+    } else {
+        if (h->W == 1) k_expect<1, double><<<grid, 256, 0, h->st>>>(a.x, (const double*)a.c, h->cap, h->n_res, h->partial);
+        else k_expect<2, double><<<grid, 256, 0, h->st>>>(a.x, (const double*)a.c, h->cap, h->n_res, h->partial);
+    }
+    CK(cudaGetLastError());
+    std::vector<__int128> part(grid);
+    CK(cudaMemcpyAsync(part.data(), h->partial, sizeof(__int128) * grid, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    __int128 tot = 0;
+    for (auto v : part) tot += v;
+    bool neg = tot < 0;
+    unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
+    long double v = (long double)(uint64_t)(mag >> 64) * 18446744073709551616.0L + (long double)(uint64_t)mag;
+    v = std::ldexp(v, -80);
+    *value = (double)(neg ? -v : v);
+    return PP_OK;
+}
+
+pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, double* c, size_t* n_out) {
+    if (!h || !n_out) return PP_ERR_ARG;
+    h->err.clear();
+    if (!h->have_result) return fail(h, PP_ERR_STATE, "no propagation result");
+    *n_out = h->n_res;
+    if (!x && !z && !c) return PP_OK;
+    if (cap < h->n_res) return fail(h, PP_ERR_CAPACITY, "export buffer holds %zu < %zu terms", cap, h->n_res);
+    const size_t N = h->n_res;
+    const int W = h->W;
+    const Arena& a = h->arena[h->res_side];
+    std::vector<uint64_t> hx(N * W), hz(N * W);
+    std::vector<double> hc(N);
+    for (int w = 0; w < W; ++w) {
+        CK(cudaMemcpyAsync(hx.data() + w * N, a.x + (size_t)w * h->cap, N * 8, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(hz.data() + w * N, a.z + (size_t)w * h->cap, N * 8, cudaMemcpyDeviceToHost, h->st));
+    }
+    if (h->opt.precision == PP_PRECISION_FP32) {
+        std::vector<float> hf(N);
+        CK(cudaMemcpyAsync(hf.data(), a.c, N * 4, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (size_t i = 0; i < N; ++i) hc[i] = hf[i];
+    } else {
+        CK(cudaMemcpyAsync(hc.data(), a.c, N * 8, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+    }
+    std::vector<size_t> idx(N);
+    for (size_t i = 0; i < N; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](size_t a_, size_t b_) {
+        for (int w = W - 1; w >= 0; --w)
+            if (hx[w * N + a_] != hx[w * N + b_]) return hx[w * N + a_] < hx[w * N + b_];
+        for (int w = W - 1; w >= 0; --w)
+            if (hz[w * N + a_] != hz[w * N + b_]) return hz[w * N + a_] < hz[w * N + b_];
+        return false;
+    });
+    for (size_t k = 0; k < N; ++k) {
+        size_t i = idx[k];
+        for (int w = 0; w < W; ++w) {
+            if (x) x[k * W + w] = hx[w * N + i];
+            if (z) z[k * W + w] = hz[w * N + i];
+        }
+        if (c) c[k] = hc[i];
+    }
+    return PP_OK;
+}
+
+pp_status pp_get_stats(const pp_handle* h, pp_stats* out) {
+    if (!h || !out) return PP_ERR_ARG;
+    *out = h->stats;
+    return PP_OK;
+}
+
+}  // extern "C"

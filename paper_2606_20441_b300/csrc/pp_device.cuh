@@ -1,0 +1,378 @@
+// Device-side core of libpp: sub-layer descriptors, per-string activity and
+// orbit keys, Pauli-product phases, and the tile processor that applies every
+// gate of one sub-layer to a bucket of strings held in shared memory.
+//
+// Method (Sec. I, Eq. evolve_gate / evolve_noise; App. G): backward propagation
+// of a Pauli sum, one gate at a time, each gate followed by truncation.  The
+// kernels reproduce that per-gate semantics exactly while reading and writing
+// each string once per *sub-layer* (a run of commuting gates of one kind):
+//
+//   * A sub-layer's gates pairwise commute, so whether gate g acts on a string
+//     (anticommutes with it) is the same for the string and for every string it
+//     can be mapped to within the sub-layer.  The set of acting gates ("activity")
+//     and the union of their supports are therefore invariant along the orbit.
+//   * Masking the string with that union gives an orbit key: strings that can
+//     ever meet (be each other's partner P xor R_g) share it.  Buckets are formed
+//     by hashing the key, so every orbit lies inside one bucket.
+//   * Inside a bucket the gates are applied in rounds: in round r each string
+//     applies the r-th gate of its own activity set, in listed order.  Orbits are
+//     independent, so this is the gate-by-gate result for every orbit at once.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pp {
+
+constexpr int MAXW = 2;          // up to 128 qubits
+constexpr int MAX_SITES = 128;
+constexpr int MAX_SEG = 4;
+constexpr int MAX_GEN = 64;      // gates in a generic sub-layer
+constexpr int FIX_SHIFT = 56;    // noise exponents in fixed point: value * 2^56
+
+enum SubClass : int {
+    CLS_NONE = 0,     // no gates (noise only, or the initial merge pass)
+    CLS_LOCAL1 = 1,   // single-qubit rotations of one letter, e.g. R_X on sites
+    CLS_LOCAL2 = 2,   // two-qubit rotations of one letter pair and one site shift, e.g. R_ZZ
+    CLS_GENERIC = 3   // anything else: up to 64 explicit generators
+};
+
+// One fused sub-layer.  For class gates the "slot" of a gate is its first site a;
+// the gate's generator is letter (ax,az) on a and, for LOCAL2, (bx,bz) on a+shift.
+// The listed (backward-application) order is: segment 0's slots ascending, then
+// segment 1's, ...  For generic sub-layers the slot is the gate index j.
+struct SubLayerDesc {
+    int cls;
+    int ax, az, bx, bz;
+    int shift;
+    int nseg;
+    int n_gates;
+    int noise;                    // index of the noise map applied before the gates, or -1
+    int first;                    // 1: input observable (merge duplicates, truncate)
+    int final_;                   // 1: last sub-layer (outputs go to the compact result)
+    int pad_;
+    uint64_t seg[MAX_SEG][MAXW];
+    uint64_t all[MAXW];           // union of segments
+    double cs[MAX_SITES];         // cos(theta) by slot
+    double sn[MAX_SITES];         // sin(theta) by slot
+    int16_t order[MAX_SITES];     // listed index of the gate in each slot
+    uint64_t gx[MAX_GEN][MAXW];   // generic generators
+    uint64_t gz[MAX_GEN][MAXW];
+};
+
+// Sparse Pauli-Lindblad map evaluated from tables.  Letter code l = x + 2z
+// (I=0, X=1, Z=2, Y=3).  Exponents are 64-bit fixed point (2^-56 units), summed
+// exactly.
+struct NoiseDesc {
+    int mode;                     // 0: exp(+2s), 1: exp(-2s)
+    int n_generic;
+    const int64_t* t1;            // [n][4]   sum of lambda over 1-local generators on q
+                                  //          anticommuting with letter l
+    const int32_t* pair_off;      // [n+1]    CSR of pairs incident to each site
+    const int32_t* pair_other;    // [2P]     other site of the pair
+    const int32_t* pair_id;       // [2P]
+    const int64_t* t2;            // [P][16]  sum over 2-local generators on (a,b), index la + 4 lb
+                                  //          (a < b), anticommuting with the letter pair
+    const uint64_t* gen_x;        // [n_generic][W] heavier generators
+    const uint64_t* gen_z;
+    const int64_t* gen_lam;
+};
+
+// ----------------------------------------------------------------------------- bit helpers
+
+__device__ __forceinline__ int popc64(uint64_t v) { return __popcll(v); }
+
+template <int W>
+__device__ __forceinline__ void shr_words(const uint64_t* v, int d, uint64_t* out) {
+    // out = v >> d as a W-word little-endian integer (0 <= d < 64*W)
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        int src = w + d / 64;
+        int sh = d % 64;
+        uint64_t lo = (src < W) ? v[src] : 0ull;
+        uint64_t hi = (src + 1 < W) ? v[src + 1] : 0ull;
+        out[w] = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void shl_words(const uint64_t* v, int d, uint64_t* out) {
+#pragma unroll
+    for (int w = W - 1; w >= 0; --w) {
+        int src = w - d / 64;
+        int sh = d % 64;
+        uint64_t hi = (src >= 0) ? v[src] : 0ull;
+        uint64_t lo = (src - 1 >= 0) ? v[src - 1] : 0ull;
+        out[w] = sh ? ((hi << sh) | (lo >> (64 - sh))) : hi;
+    }
+}
+
+// Position of the r-th (0-based) set bit of v; v must have more than r set bits.
+__device__ __forceinline__ int select64(uint64_t v, int r) {
+    unsigned lo = (unsigned)v;
+    int c = __popc(lo);
+    if (r < c) return __fns(lo, 0, r + 1);
+    return 32 + __fns((unsigned)(v >> 32), 0, r - c + 1);
+}
+
+// Power of i in R * S = i^e (R xor S) for Hermitian Pauli strings (Y = i X Z):
+// per qubit e = r_x r_z + s_x s_z + 2 r_z s_x - (r_x^s_x)(r_z^s_z)  (mod 4).
+template <int W>
+__device__ __forceinline__ int product_phase(const uint64_t* rx, const uint64_t* rz,
+                                             const uint64_t* sx, const uint64_t* sz) {
+    int e = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        e += popc64(rx[w] & rz[w]) + popc64(sx[w] & sz[w]) + 2 * popc64(rz[w] & sx[w]) -
+             popc64((rx[w] ^ sx[w]) & (rz[w] ^ sz[w]));
+    }
+    return e & 3;
+}
+
+template <int W>
+__device__ __forceinline__ int anticommutes(const uint64_t* px, const uint64_t* pz,
+                                            const uint64_t* rx, const uint64_t* rz) {
+    int s = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) s += popc64((px[w] & rz[w]) ^ (pz[w] & rx[w]));
+    return s & 1;
+}
+
+template <int W>
+__device__ __forceinline__ int weight_of(const uint64_t* x, const uint64_t* z) {
+    int s = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) s += popc64(x[w] | z[w]);
+    return s;
+}
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdULL;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ULL;
+    h ^= h >> 33;
+    return h;
+}
+
+template <int W>
+__device__ __forceinline__ uint64_t hash_key(const uint64_t* x, const uint64_t* z) {
+    uint64_t h = 0x9e3779b97f4a7c15ULL;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        h = fmix64(h ^ x[w]);
+        h = fmix64(h ^ (z[w] + 0x632be59bd9b4e019ULL));
+    }
+    return h;
+}
+
+// ----------------------------------------------------------------------------- activity
+
+// Activity of string (x,z) in a sub-layer: bit per slot whose gate anticommutes
+// with the string.  Also the union of the acting generators' supports (per
+// letter bit), which masks the string into its orbit key.
+template <int W>
+__device__ __forceinline__ void activity(const SubLayerDesc& d, const uint64_t* x,
+                                         const uint64_t* z, uint64_t* A, uint64_t* Mx,
+                                         uint64_t* Mz) {
+    if (d.cls == CLS_LOCAL1 || d.cls == CLS_LOCAL2) {
+        uint64_t fa[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) fa[w] = (d.ax ? z[w] : 0ull) ^ (d.az ? x[w] : 0ull);
+        if (d.cls == CLS_LOCAL1) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                A[w] = fa[w] & d.all[w];
+                Mx[w] = d.ax ? A[w] : 0ull;
+                Mz[w] = d.az ? A[w] : 0ull;
+            }
+        } else {
+            uint64_t fb[W], fbs[W], As[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) fb[w] = (d.bx ? z[w] : 0ull) ^ (d.bz ? x[w] : 0ull);
+            shr_words<W>(fb, d.shift, fbs);
+#pragma unroll
+            for (int w = 0; w < W; ++w) A[w] = (fa[w] ^ fbs[w]) & d.all[w];
+            shl_words<W>(A, d.shift, As);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                Mx[w] = (d.ax ? A[w] : 0ull) | (d.bx ? As[w] : 0ull);
+                Mz[w] = (d.az ? A[w] : 0ull) | (d.bz ? As[w] : 0ull);
+            }
+        }
+    } else if (d.cls == CLS_GENERIC) {
+        uint64_t a = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) Mx[w] = Mz[w] = 0ull;
+        for (int j = 0; j < d.n_gates; ++j) {
+            if (anticommutes<W>(x, z, d.gx[j], d.gz[j])) {
+                a |= 1ull << j;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    Mx[w] |= d.gx[j][w] | d.gz[j][w];
+                    Mz[w] |= d.gx[j][w] | d.gz[j][w];
+                }
+            }
+        }
+        A[0] = a;
+#pragma unroll
+        for (int w = 1; w < W; ++w) A[w] = 0ull;
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) A[w] = Mx[w] = Mz[w] = 0ull;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ int count_active(const uint64_t* A) {
+    int k = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) k += popc64(A[w]);
+    return k;
+}
+
+// Slot of the r-th acting gate (listed order) for activity A.
+template <int W>
+__device__ __forceinline__ int select_slot(const SubLayerDesc& d, const uint64_t* A, int r) {
+    if (d.cls == CLS_GENERIC) return select64(A[0], r);
+    for (int s = 0; s < d.nseg; ++s) {
+        uint64_t As[W];
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            As[w] = A[w] & d.seg[s][w];
+            cnt += popc64(As[w]);
+        }
+        if (r < cnt) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                int c = popc64(As[w]);
+                if (r < c) return 64 * w + select64(As[w], r);
+                r -= c;
+            }
+        }
+        r -= cnt;
+    }
+    return -1;
+}
+
+// Generator (rx, rz) of the gate in `slot`.
+template <int W>
+__device__ __forceinline__ void slot_generator(const SubLayerDesc& d, int slot, uint64_t* rx,
+                                               uint64_t* rz) {
+    if (d.cls == CLS_GENERIC) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            rx[w] = d.gx[slot][w];
+            rz[w] = d.gz[slot][w];
+        }
+        return;
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) rx[w] = rz[w] = 0ull;
+    int a = slot;
+    uint64_t bit = 1ull << (a & 63);
+    if (d.ax) rx[a >> 6] |= bit;
+    if (d.az) rz[a >> 6] |= bit;
+    if (d.cls == CLS_LOCAL2) {
+        int b = a + d.shift;
+        uint64_t bb = 1ull << (b & 63);
+        if (d.bx) rx[b >> 6] |= bb;
+        if (d.bz) rz[b >> 6] |= bb;
+    }
+}
+
+// Orbit key of a string for sub-layer d and its bucket under 2^log2b buckets.
+template <int W>
+__device__ __forceinline__ uint32_t bucket_of(const SubLayerDesc& d, const uint64_t* x,
+                                              const uint64_t* z, uint32_t bmask) {
+    uint64_t A[W], Mx[W], Mz[W], kx[W], kz[W];
+    activity<W>(d, x, z, A, Mx, Mz);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        kx[w] = x[w] & ~Mx[w];
+        kz[w] = z[w] & ~Mz[w];
+    }
+    return (uint32_t)(hash_key<W>(kx, kz) >> 20) & bmask;
+}
+
+// ----------------------------------------------------------------------------- noise
+
+template <int W>
+__device__ __forceinline__ int64_t noise_exponent(const NoiseDesc& nz, const uint64_t* x,
+                                                  const uint64_t* z) {
+    int64_t s = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint64_t sup = x[w] | z[w];
+        while (sup) {
+            int b = __ffsll((long long)sup) - 1;
+            sup &= sup - 1;
+            int q = 64 * w + b;
+            int lq = (int)((x[w] >> b) & 1ull) + 2 * (int)((z[w] >> b) & 1ull);
+            s += nz.t1[4 * q + lq];
+            for (int e = nz.pair_off[q]; e < nz.pair_off[q + 1]; ++e) {
+                int o = nz.pair_other[e];
+                int lo = (int)((x[o >> 6] >> (o & 63)) & 1ull) + 2 * (int)((z[o >> 6] >> (o & 63)) & 1ull);
+                if (lo != 0 && o < q) continue;      // pair already counted at its smaller site
+                int pid = nz.pair_id[e];
+                int idx = (q < o) ? (lq + 4 * lo) : (lo + 4 * lq);
+                s += nz.t2[16 * pid + idx];
+            }
+        }
+    }
+    for (int k = 0; k < nz.n_generic; ++k)
+        if (anticommutes<W>(x, z, nz.gen_x + (size_t)k * W, nz.gen_z + (size_t)k * W))
+            s += nz.gen_lam[k];
+    return s;
+}
+
+__device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t s) {
+    double sd = (double)s * 0x1p-56;
+    return nz.mode == 0 ? exp(__dmul_rn(2.0, sd)) : exp(__dmul_rn(-2.0, sd));
+}
+
+// ----------------------------------------------------------------------------- coefficient ops
+
+template <typename T> struct Coef;
+
+template <> struct Coef<double> {
+    __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    // cs*c + phi*(sn*c2): exactly the oracle's two contributions, no fused multiply-add
+    __device__ static __forceinline__ double rot(double cs, double c, double sn, double c2, int phi) {
+        double t = __dmul_rn(sn, c2);
+        return __dadd_rn(__dmul_rn(cs, c), phi > 0 ? t : -t);
+    }
+    __device__ static __forceinline__ bool small(double c, double eps) {
+        // |c| < eps or c == 0 by the IEEE ordering of magnitudes
+        uint64_t m = (uint64_t)__double_as_longlong(c) & 0x7fffffffffffffffULL;
+        uint64_t e = (uint64_t)__double_as_longlong(eps) & 0x7fffffffffffffffULL;
+        return m == 0 || m < e;
+    }
+};
+
+template <> struct Coef<float> {
+    __device__ static __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    // Compensated cs*c + phi*sn*c2: error-free products (FMA residuals) and an
+    // error-free sum, folded into one final rounding (Ogita-Rump-Oishi Dot2).
+    __device__ static __forceinline__ float rot(float cs, float c, float sn, float c2, int phi) {
+        float p1 = __fmul_rn(cs, c);
+        float e1 = __fmaf_rn(cs, c, -p1);
+        float s2 = phi > 0 ? sn : -sn;
+        float p2 = __fmul_rn(s2, c2);
+        float e2 = __fmaf_rn(s2, c2, -p2);
+        float s = __fadd_rn(p1, p2);
+        float bp = __fsub_rn(s, p1);
+        float e3 = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bp)), __fsub_rn(p2, bp));
+        return __fadd_rn(s, __fadd_rn(e3, __fadd_rn(e1, e2)));
+    }
+    __device__ static __forceinline__ bool small(float c, float eps) {
+        uint32_t m = (uint32_t)__float_as_uint(c) & 0x7fffffffu;
+        uint32_t e = (uint32_t)__float_as_uint(eps) & 0x7fffffffu;
+        return m == 0 || m < e;
+    }
+};
+
+}  // namespace pp

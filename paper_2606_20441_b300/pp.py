@@ -1,0 +1,230 @@
+"""Thin ctypes binding of libpp (include/pp.h): the same entry points, argument
+marshalling only.  Every step of the propagation runs in the library's CUDA
+kernels; there is no CPU fallback: if libpp.so is missing or no GPU is
+present, the calls raise.
+
+PyTorch supplies device memory and streams: `Handle(..., torch_memory=True)`
+routes the library's device allocations through torch's caching allocator and
+runs on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpp.so")
+
+PP_OK, PP_ERR_ARG, PP_ERR_STATE, PP_ERR_NOMEM, PP_ERR_CAPACITY, PP_ERR_CUDA, PP_ERR_TIMEOUT = range(7)
+STATUS_NAMES = {0: "PP_OK", 1: "PP_ERR_ARG", 2: "PP_ERR_STATE", 3: "PP_ERR_NOMEM",
+                4: "PP_ERR_CAPACITY", 5: "PP_ERR_CUDA", 6: "PP_ERR_TIMEOUT"}
+PRECISION_FP64, PRECISION_FP32 = 64, 32
+NOISE_INVERSE, NOISE_FORWARD = 0, 1
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class pp_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int),
+                ("max_terms", ctypes.c_size_t),
+                ("alloc", ALLOC_FN),
+                ("free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class pp_stats(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_size_t),
+                ("peak_terms", ctypes.c_size_t),
+                ("updates", ctypes.c_double),
+                ("n_sublayers", ctypes.c_int),
+                ("kernel_launches", ctypes.c_int),
+                ("fallback_buckets", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+EXPORTED = ["pp_default_options", "pp_create", "pp_destroy", "pp_load_circuit", "pp_load_noise",
+            "pp_propagate", "pp_expect", "pp_export_terms", "pp_get_stats", "pp_last_error"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libpp.so (raises OSError if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libpp.so not built at %s (run paper_2606_20441_b300.build.build())" % path)
+    L = ctypes.CDLL(path)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    L.pp_default_options.argtypes = [ctypes.POINTER(pp_options)]
+    L.pp_default_options.restype = None
+    L.pp_create.argtypes = [ctypes.POINTER(pp_options), ctypes.c_int, ctypes.POINTER(vp)]
+    L.pp_destroy.argtypes = [vp]
+    L.pp_load_circuit.argtypes = [vp, sz, vp, vp, vp, vp, ctypes.c_int]
+    L.pp_load_noise.argtypes = [vp, ctypes.c_int, sz, vp, vp, vp, ctypes.c_int]
+    L.pp_propagate.argtypes = [vp, sz, vp, vp, vp, ctypes.c_double, ctypes.c_int]
+    L.pp_expect.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.pp_export_terms.argtypes = [vp, sz, vp, vp, vp, ctypes.POINTER(sz)]
+    L.pp_get_stats.argtypes = [vp, ctypes.POINTER(pp_stats)]
+    L.pp_last_error.argtypes = [vp]
+    L.pp_last_error.restype = ctypes.c_char_p
+    for f in EXPORTED:
+        if f not in ("pp_default_options", "pp_last_error"):
+            getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Handle:
+    """One pp_handle: a circuit, its noise maps, and the last propagation."""
+
+    def __init__(self, n_qubits: int, precision: int = PRECISION_FP64, max_terms: int = 0,
+                 torch_memory: bool = False, stream: Optional[int] = None):
+        self.L = load_library()
+        self.n_qubits = n_qubits
+        self.W = inputs.n_words(n_qubits)
+        opt = pp_options()
+        self.L.pp_default_options(ctypes.byref(opt))
+        opt.precision = precision
+        opt.max_terms = max_terms
+        self._cb = None
+        if torch_memory:
+            import torch
+            dev = torch.cuda.current_device()
+            st = torch.cuda.current_stream() if stream is None else None
+
+            def _alloc(nbytes, ctx):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            opt.alloc, opt.free = self._cb
+            opt.cuda_stream = st.cuda_stream if st is not None else stream
+        elif stream is not None:
+            opt.cuda_stream = stream
+        h = ctypes.c_void_p()
+        st_ = self.L.pp_create(ctypes.byref(opt), n_qubits, ctypes.byref(h))
+        if st_ != PP_OK:
+            raise PPError(st_, "pp_create failed")
+        self.h = h
+
+    def _check(self, status: int):
+        if status != PP_OK:
+            raise PPError(status, self.L.pp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pp_load_circuit(self, rx: np.ndarray, rz: np.ndarray, theta: np.ndarray,
+                        layer_of: np.ndarray, n_layers: int):
+        rx = np.ascontiguousarray(rx, dtype=np.uint64)
+        rz = np.ascontiguousarray(rz, dtype=np.uint64)
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        layer_of = np.ascontiguousarray(layer_of, dtype=np.int32)
+        self._check(self.L.pp_load_circuit(self.h, len(theta), _p(rx), _p(rz), _p(theta),
+                                           _p(layer_of), int(n_layers)))
+
+    def pp_load_noise(self, layer: int, ex: np.ndarray, ez: np.ndarray, lam: np.ndarray,
+                      mode: int = NOISE_INVERSE):
+        ex = np.ascontiguousarray(ex, dtype=np.uint64)
+        ez = np.ascontiguousarray(ez, dtype=np.uint64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self._check(self.L.pp_load_noise(self.h, int(layer), len(lam), _p(ex), _p(ez), _p(lam),
+                                         int(mode)))
+
+    def pp_propagate(self, ox: np.ndarray, oz: np.ndarray, oc: np.ndarray, eps: float = 0.0,
+                     w_max: int = -1):
+        ox = np.ascontiguousarray(ox, dtype=np.uint64)
+        oz = np.ascontiguousarray(oz, dtype=np.uint64)
+        oc = np.ascontiguousarray(oc, dtype=np.float64)
+        self._check(self.L.pp_propagate(self.h, len(oc), _p(ox), _p(oz), _p(oc), float(eps),
+                                        int(w_max)))
+
+    def pp_expect(self) -> float:
+        v = ctypes.c_double()
+        self._check(self.L.pp_expect(self.h, ctypes.byref(v)))
+        return v.value
+
+    def pp_export_terms(self):
+        n = ctypes.c_size_t()
+        self._check(self.L.pp_export_terms(self.h, 0, None, None, None, ctypes.byref(n)))
+        N = n.value
+        x = np.zeros((N, self.W), dtype=np.uint64)
+        z = np.zeros((N, self.W), dtype=np.uint64)
+        c = np.zeros(N, dtype=np.float64)
+        self._check(self.L.pp_export_terms(self.h, N, _p(x), _p(z), _p(c), ctypes.byref(n)))
+        return x, z, c
+
+    def pp_get_stats(self) -> pp_stats:
+        s = pp_stats()
+        self._check(self.L.pp_get_stats(self.h, ctypes.byref(s)))
+        return s
+
+    # convenience: a whole Instance
+    def load_instance(self, inst: "inputs.Instance"):
+        assert inst.n_qubits == self.n_qubits
+        self.pp_load_circuit(inst.gate_x, inst.gate_z, inst.theta, inst.layer_of, inst.n_layers)
+        for m in inst.noise:
+            self.pp_load_noise(m.layer, m.ex, m.ez, m.lam, m.mode)
+
+    def run_instance(self, inst: "inputs.Instance", eps: Optional[float] = None,
+                     w_max: Optional[int] = None):
+        self.pp_propagate(inst.obs_x, inst.obs_z, inst.obs_c,
+                          inst.eps if eps is None else eps,
+                          inst.w_max if w_max is None else w_max)
+
+
+@dataclasses.dataclass
+class Result:
+    x: np.ndarray
+    z: np.ndarray
+    c: np.ndarray
+    expect: float
+    stats: pp_stats
+
+
+def propagate(inst: "inputs.Instance", precision: int = PRECISION_FP64, max_terms: int = 0,
+              export: bool = True, eps: Optional[float] = None,
+              w_max: Optional[int] = None) -> Result:
+    """One-shot: load, propagate, expectation (and the exported terms)."""
+    h = Handle(inst.n_qubits, precision=precision, max_terms=max_terms)
+    try:
+        h.load_instance(inst)
+        h.run_instance(inst, eps, w_max)
+        e = h.pp_expect()
+        if export:
+            x, z, c = h.pp_export_terms()
+        else:
+            x = z = c = None
+        return Result(x, z, c, e, h.pp_get_stats())
+    finally:
+        h.close()
