@@ -1,0 +1,345 @@
+"""Benchmark: noisy-inverse Pauli propagation on B300.
+
+A step is one whole backward propagation of the workload's observable through
+every layer (R_X layer, inverse noise, R_ZZ layer per Trotter step, with
+truncation) plus the expectation on |0..0>.  Metric: Pauli-term updates per
+second, the canonical gate-by-gate count (sum over gates of the live terms
+entering the gate).
+
+Workload (default): 7x8 open-boundary TFIM, 56 qubits, 20 Trotter steps,
+R_ZZ(0.3), R_X(0.6), observable the mean of Z_a Z_b over the 97 edges, rates
+uniform [0, 1e-3), weight cap 10, threshold 1e-6 -- the smallest threshold of
+its 1e-4..1e-7 sweep that fits one GPU -- in the FP32-coefficient form.  The
+6x6 / 10-step FP64 workload needs about 1e10 live strings (more than a B300
+holds) and is not a single-GPU configuration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun) are independent replicas: every rank propagates the
+same workload, no data-path collective; value = updates of all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2606_20441_b300 import inputs  # noqa: E402
+
+METRIC = "Pauli-term updates/s"
+UNIT = "updates/s"
+PROFILE = os.path.join(ROOT, "profiles", "k_process_tfim7x8.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2606_20441_b300", "csrc", f)
+                  for f in ("pp_device.cuh", "pp_kernels.cuh")]
+
+
+def workload(args):
+    if args.workload == "tfim7x8":
+        return inputs.workload_7x8(eps=args.eps, w_max=10)
+    if args.workload == "tfim6x6":
+        return inputs.workload_6x6(eps=args.eps)
+    raise SystemExit("unknown workload " + args.workload)
+
+
+def oracle_sample(args, steps):
+    """The same workload family cut to its first `steps` Trotter steps (same
+    seed, same per-step rates): a bounded sample for the CPU oracle."""
+    if args.workload == "tfim7x8":
+        return inputs.workload_7x8(eps=args.eps, w_max=10, steps=steps)
+    return inputs.workload_6x6(eps=args.eps, steps=steps)
+
+
+def config_of(args, inst):
+    m = inst.meta
+    return {"workload": "%s_s%d_eps%g_wmax%d" % (args.workload, m["steps"], args.eps, inst.w_max),
+            "lattice": "%dx%d" % (m["rows"], m["cols"]), "qubits": inst.n_qubits,
+            "trotter_steps": m["steps"], "eps": args.eps, "w_max": inst.w_max,
+            "coefficients": "fp%d" % args.precision, "noise": "inverse sparse Pauli-Lindblad, "
+            "3n + 9|E| generators per step", "l2": "working set (>1 GB of strings) larger than L2",
+            "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(strings_per_launch, precision):
+    """DRAM bytes per launch of the main-tier kernel from the committed ncu
+    summary, scaled by strings processed, or None when the kernel source
+    changed since the counters were taken."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"dram_bytes_per_string_fp%d:\s*([0-9.eE+]+)" % precision, txt)
+    if not m_sha or not m_tr or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_tr.group(1)) * strings_per_launch
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def run_oracle_sample(args, steps):
+    from oracle import oracle
+    inst = oracle_sample(args, steps)
+    t = time.perf_counter()
+    r = oracle.run(inst)
+    return r.updates, time.perf_counter() - t
+
+
+# ----------------------------------------------------------------------------- arms
+
+def reference_arm(args, rank, world):
+    """The CPU oracle as it stands, on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    inst = workload(args)
+    for _ in range(args.warmup):
+        run_oracle_sample(args, 1)
+    upd, sec = 0.0, 0.0
+    for _ in range(args.steps):
+        u, s = run_oracle_sample(args, args.sample_steps)
+        upd += u
+        sec += s
+    v = upd / sec
+    sample = ("%s cut to its first %d Trotter steps per timed step (warm-up steps: first 1 step); "
+              "single-threaded FP64 hash-map oracle" % (args.workload, args.sample_steps))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, inst), "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ours_arm(args, rank, world, local_rank):
+    import torch
+    from paper_2606_20441_b300 import build, pp
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    inst = workload(args)
+    h = pp.Handle(inst.n_qubits, precision=args.precision)
+    h.load_instance(inst)
+    for _ in range(args.warmup):
+        h.run_instance(inst)
+        h.pp_expect()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    phys = int(vis.split(",")[local_rank]) if vis and vis.split(",")[local_rank].isdigit() else local_rank
+    clocks = ClockSampler(phys)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    updates, launches = 0.0, 0
+    tier_ms = [0.0, 0.0, 0.0]
+    tier_strings = [0.0, 0.0, 0.0]
+    tier_launches = [0, 0, 0]
+    expect = None
+    for _ in range(args.steps):
+        h.run_instance(inst)
+        expect = h.pp_expect()
+        s = h.pp_get_stats()
+        updates += s.updates
+        launches += s.kernel_launches
+        for t in range(3):
+            tier_ms[t] += s.tier_ms[t]
+            tier_strings[t] += s.tier_strings[t]
+            tier_launches[t] += s.tier_launches[t]
+        bps = s.bytes_per_string
+        n_terms, peak = s.n_terms, s.peak_terms
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = e0.elapsed_time(e1) / 1000.0
+    tot_updates = updates
+    if dist:
+        t = torch.tensor([sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+        u = torch.tensor([updates], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u)
+        tot_updates = float(u.item())
+
+    # end-to-end through the C ABI with host buffers: load circuit and noise,
+    # propagate the host observable, read the expectation back, every step
+    h2d = (inst.gate_x.nbytes + inst.gate_z.nbytes + inst.theta.nbytes + inst.layer_of.nbytes +
+           sum(m.ex.nbytes + m.ez.nbytes + m.lam.nbytes for m in inst.noise) +
+           inst.obs_x.nbytes + inst.obs_z.nbytes + inst.obs_c.nbytes)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_upd = 0.0
+    for _ in range(args.steps):
+        h.load_instance(inst)
+        h.run_instance(inst)
+        h.pp_expect()
+        e2e_upd += h.pp_get_stats().updates
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+        e2e_upd *= world
+
+    # FP32 form against the FP64 form on the same workload (FP64 final sums in both)
+    err = None
+    if args.precision == 32 and rank == 0 and not args.no_fp64_check:
+        h64 = pp.Handle(inst.n_qubits, precision=64)
+        h64.load_instance(inst)
+        h64.run_instance(inst)
+        err = abs(expect - h64.pp_expect())
+        h64.close()
+    h.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak_gbs, peak_kind = read_peaks()
+    main_ms_avg = tier_ms[0] / max(1, tier_launches[0])
+    main_bytes = tier_strings[0] * bps / max(1, tier_launches[0])
+    achieved = main_bytes / (main_ms_avg / 1000.0) / 1e9 if main_ms_avg > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "k_process (main shared-memory tier)",
+                "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": main_bytes, "avg_launch_ms": main_ms_avg,
+                "traffic": profiled_traffic(tier_strings[0] / max(1, tier_launches[0]), args.precision),
+                "share_of_step_time": (tier_ms[0] / 1000.0) / sec if sec > 0 else None}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        u, s_ = run_oracle_sample(args, args.sample_steps)
+        cpu = {"value": u / s_, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%s cut to its first %d Trotter steps (%.3g updates in %.1f s), "
+                         "single-threaded FP64 hash-map oracle" % (args.workload, args.sample_steps, u, s_)}
+    line = {"metric": METRIC, "value": tot_updates / sec, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f%d" % args.precision, "data": "synthetic", "config": config_of(args, inst),
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_upd / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": 8},
+            "clocks": clk, "gpu_launches": launches,
+            "result": {"expect": expect, "terms": int(n_terms), "peak_terms": int(peak),
+                       "updates_per_step": updates / args.steps,
+                       "fp32_abs_err_vs_fp64": err},
+            "tiers_ms_per_step": [m / args.steps for m in tier_ms]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="tfim7x8")
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--precision", type=int, choices=[32, 64], default=32)
+    ap.add_argument("--sample-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        ours_arm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -19,9 +19,11 @@ using namespace pp;
 namespace {
 
 constexpr int kThreads = 512;
-constexpr int kTileCap1 = 2048;   // shared-memory tile entries, W = 1
+constexpr int kTileCap1 = 2048;   // main shared-memory tile entries, W = 1
 constexpr int kTileCap2 = 1024;   // W = 2
-constexpr int kFallbackCTAs = 16;
+constexpr int kBigCap1 = 4096;    // large shared-memory tier (one CTA per SM)
+constexpr int kBigCap2 = 2048;
+constexpr int kFallbackCTAs = 32; // global-memory tier
 constexpr int kFallbackCap = 1 << 20;
 
 struct NoiseHost {
@@ -76,7 +78,13 @@ struct pp_handle {
     uint32_t fill_cap = 0;
     unsigned long long* counters = nullptr;
     long long* delta = nullptr;
-    uint32_t* deferred = nullptr;
+    uint32_t* list_a = nullptr;    // buckets passed main -> large tier
+    uint32_t* list_b = nullptr;    // buckets passed large -> global tier
+    size_t spill_cap = 0;          // overflow strings per layout
+    Arena spill_raw, spill_grp;
+    uint32_t* spill_b = nullptr;
+    uint32_t* spill_s = nullptr;
+    uint64_t* soff[2] = {nullptr, nullptr};
     unsigned char* fb_scratch = nullptr;
     size_t fb_slice = 0;
     uint64_t* stage = nullptr;     // input staging
@@ -314,6 +322,20 @@ size_t tile_smem(const pp_handle* h) {
     return per * (size_t)tile_cap(h);
 }
 
+size_t tile_entry_bytes(const pp_handle* h) {
+    return h->opt.precision == PP_PRECISION_FP32
+               ? (h->W == 1 ? tile_bytes_per_entry<1, float>() : tile_bytes_per_entry<2, float>())
+               : (h->W == 1 ? tile_bytes_per_entry<1, double>() : tile_bytes_per_entry<2, double>());
+}
+
+pp_status alloc_arena(pp_handle* h, Arena* a, size_t cap) {
+    a->x = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
+    a->z = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
+    a->c = dev_alloc(h, cap * (h->opt.precision == PP_PRECISION_FP32 ? 4 : 8));
+    if (!a->x || !a->z || !a->c) return fail(h, PP_ERR_NOMEM, "term arena allocation (%zu terms) failed", cap);
+    return PP_OK;
+}
+
 pp_status ensure_memory(pp_handle* h) {
     if (h->arena[0].x) return PP_OK;
     size_t tb = term_bytes(h);
@@ -321,33 +343,34 @@ pp_status ensure_memory(pp_handle* h) {
     if (cap == 0) {
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
-        // two arenas take at most 60% of free memory
-        cap = (size_t)(0.30 * (double)fr) / tb;
+        // two term arenas and two overflow areas of a quarter arena: ~62% of free memory
+        cap = (size_t)(0.25 * (double)fr) / tb;
     }
     cap = std::max<size_t>(cap, 4096);
     h->cap = cap;
-    for (int s = 0; s < 2; ++s) {
-        h->arena[s].x = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
-        h->arena[s].z = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
-        h->arena[s].c = dev_alloc(h, cap * (h->opt.precision == PP_PRECISION_FP32 ? 4 : 8));
-        if (!h->arena[s].x || !h->arena[s].z || !h->arena[s].c)
-            return fail(h, PP_ERR_NOMEM, "term arena allocation (%zu terms) failed", cap);
-    }
+    pp_status st;
+    for (int s = 0; s < 2; ++s)
+        if ((st = alloc_arena(h, &h->arena[s], cap)) != PP_OK) return st;
+    h->spill_cap = std::max<size_t>(cap / 4, 4096);
+    if ((st = alloc_arena(h, &h->spill_raw, h->spill_cap)) != PP_OK) return st;
+    if ((st = alloc_arena(h, &h->spill_grp, h->spill_cap)) != PP_OK) return st;
+    h->spill_b = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
+    h->spill_s = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
     h->fill_cap = (uint32_t)std::min<size_t>(std::max<size_t>(cap / 64, 1024), 1u << 28);
     for (int s = 0; s < 2; ++s) {
         h->fill[s] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
-        if (!h->fill[s]) return fail(h, PP_ERR_NOMEM, "bucket counters allocation failed");
+        h->soff[s] = static_cast<uint64_t*>(dev_alloc(h, sizeof(uint64_t) * h->fill_cap));
+        if (!h->fill[s] || !h->soff[s]) return fail(h, PP_ERR_NOMEM, "bucket counters allocation failed");
     }
     h->counters = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * CTR_COUNT));
     h->delta = static_cast<long long*>(dev_alloc(h, sizeof(long long) * MAX_SITES));
-    h->deferred = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
+    h->list_a = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
+    h->list_b = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
     h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * 4096));
-    size_t per = h->opt.precision == PP_PRECISION_FP32
-                     ? (h->W == 1 ? tile_bytes_per_entry<1, float>() : tile_bytes_per_entry<2, float>())
-                     : (h->W == 1 ? tile_bytes_per_entry<1, double>() : tile_bytes_per_entry<2, double>());
-    h->fb_slice = (per * kFallbackCap + 255) & ~(size_t)255;
+    h->fb_slice = (tile_entry_bytes(h) * kFallbackCap + 255) & ~(size_t)255;
     h->fb_scratch = static_cast<unsigned char*>(dev_alloc(h, h->fb_slice * kFallbackCTAs));
-    if (!h->counters || !h->delta || !h->deferred || !h->partial || !h->fb_scratch)
+    if (!h->spill_b || !h->spill_s || !h->counters || !h->delta || !h->list_a || !h->list_b ||
+        !h->partial || !h->fb_scratch)
         return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     return PP_OK;
 }
@@ -358,35 +381,43 @@ uint32_t pow2_at_least(double v, uint32_t cap) {
     return b;
 }
 
+enum Tier { TIER_MAIN = 0, TIER_LARGE = 1, TIER_GLOBAL = 2 };
+
 template <int W, typename T>
-cudaError_t launch_process(pp_handle* h, const StepParams& p, bool fallback, uint32_t n_def, int* launches) {
-    if (!fallback) {
-        int cap = W == 1 ? kTileCap1 : kTileCap2;
+cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t n_items, int* launches) {
+    if (tier == TIER_GLOBAL) {
+        uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)kFallbackCTAs);
+        k_process_global<W, T><<<grid, kThreads, 0, h->st>>>(p, h->fb_scratch, h->fb_slice, kFallbackCap);
+    } else {
+        int cap = tier == TIER_MAIN ? (W == 1 ? kTileCap1 : kTileCap2) : (W == 1 ? kBigCap1 : kBigCap2);
         size_t smem = tile_bytes_per_entry<W, T>() * (size_t)cap;
-        static bool attr_set = false;
-        if (!attr_set) {
+        static int attr_set = 0;
+        if (attr_set < (int)smem) {
             cudaFuncSetAttribute(k_process<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set = true;
+            attr_set = (int)smem;
         }
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T>, kThreads, smem);
         per_sm = std::max(per_sm, 1);
-        uint32_t grid = std::min<uint32_t>(p.sB, (uint32_t)(per_sm * h->sm_count));
+        uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(per_sm * h->sm_count));
         k_process<W, T><<<grid, kThreads, smem, h->st>>>(p, cap);
-    } else {
-        uint32_t grid = std::min<uint32_t>(n_def, (uint32_t)kFallbackCTAs);
-        k_process_global<W, T><<<grid, kThreads, 0, h->st>>>(p, h->fb_scratch, h->fb_slice, kFallbackCap, n_def);
     }
     ++*launches;
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_process(pp_handle* h, const StepParams& p, bool fb, uint32_t n_def, int* launches) {
+int tier_cap(const pp_handle* h, int tier) {
+    if (tier == TIER_MAIN) return h->W == 1 ? kTileCap1 : kTileCap2;
+    if (tier == TIER_LARGE) return h->W == 1 ? kBigCap1 : kBigCap2;
+    return kFallbackCap;
+}
+
+cudaError_t dispatch_process(pp_handle* h, const StepParams& p, int tier, uint32_t n_items, int* launches) {
     bool f32 = h->opt.precision == PP_PRECISION_FP32;
-    if (h->W == 1) return f32 ? launch_process<1, float>(h, p, fb, n_def, launches)
-                              : launch_process<1, double>(h, p, fb, n_def, launches);
-    return f32 ? launch_process<2, float>(h, p, fb, n_def, launches)
-               : launch_process<2, double>(h, p, fb, n_def, launches);
+    if (h->W == 1) return f32 ? launch_process<1, float>(h, p, tier, n_items, launches)
+                              : launch_process<1, double>(h, p, tier, n_items, launches);
+    return f32 ? launch_process<2, float>(h, p, tier, n_items, launches)
+               : launch_process<2, double>(h, p, tier, n_items, launches);
 }
 
 cudaError_t dispatch_scatter(pp_handle* h, const uint64_t* ox, const uint64_t* oz, const double* oc,
@@ -402,6 +433,28 @@ cudaError_t dispatch_scatter(pp_handle* h, const uint64_t* ox, const uint64_t* o
         else k_scatter_input<2, double><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
     }
     ++*launches;
+    return cudaGetLastError();
+}
+
+// Groups the overflow strings of a freshly written layout by bucket.
+cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, uint64_t n_spill, int* launches) {
+    if (n_spill == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(h->counters + CTR_COUNT - 1, 0, sizeof(unsigned long long), h->st);
+    if (e != cudaSuccess) return e;
+    uint32_t grid = (nB + 1023) / 1024;
+    k_spill_offsets<<<grid, 1024, 0, h->st>>>(h->fill[side], nB, C, h->soff[side], h->counters + CTR_COUNT - 1);
+    int g2 = (int)std::min<uint64_t>((n_spill + 255) / 256, 8192);
+    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    const Arena& r = h->spill_raw;
+    const Arena& o = h->spill_grp;
+    if (h->W == 1) {
+        if (f32) k_spill_move<1, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
+        else k_spill_move<1, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
+    } else {
+        if (f32) k_spill_move<2, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
+        else k_spill_move<2, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
+    }
+    *launches += 2;
     return cudaGetLastError();
 }
 
@@ -638,11 +691,11 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     if (h->subs_dirty && (st = build_plan(h)) != PP_OK) return st;
     if ((st = ensure_memory(h)) != PP_OK) return st;
     const int W = h->W;
-    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
     int launches = 0;
     pp_stats stats{};
 
     // stage the observable
+    if (n_terms > h->cap) return fail(h, PP_ERR_CAPACITY, "observable larger than capacity");
     size_t need = std::max<size_t>(n_terms, 1) * (2 * W + 1);
     if (need > h->stage_cap) {
         if (h->stage) dev_free(h, h->stage);
@@ -650,7 +703,6 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         if (!h->stage) return fail(h, PP_ERR_NOMEM, "staging allocation failed");
         h->stage_cap = need;
     }
-    if (n_terms > h->cap) return fail(h, PP_ERR_CAPACITY, "observable larger than capacity");
     uint64_t* sx = h->stage;
     uint64_t* sz = h->stage + n_terms * W;
     double* sc = reinterpret_cast<double*>(h->stage + 2 * n_terms * W);
@@ -660,14 +712,32 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         CK(cudaMemcpyAsync(sc, oc, n_terms * 8, cudaMemcpyHostToDevice, h->st));
     }
 
-    const size_t tcap = (size_t)tile_cap(h);
-    const double target = (double)tcap / 6.0;    // expected input strings per bucket
-    std::map<int, double> growth;                // observed output/input per sub-layer kind
-    int side = 0;
-    uint32_t B = pow2_at_least((double)n_terms / target, h->fill_cap);
-    uint64_t C = h->cap / B;
-    CK(cudaMemsetAsync(h->fill[side], 0, sizeof(uint32_t) * B, h->st));
-    CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+    struct Scope {
+        FILE* trace = nullptr;
+        cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        ~Scope() {
+            if (trace) fclose(trace);
+            for (auto e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } scope;
+    if (const char* tp = getenv("PP_TRACE")) scope.trace = fopen(tp, "a");
+    FILE* trace = scope.trace;
+    for (auto& e : scope.ev) CK(cudaEventCreate(&e));
+
+    const size_t tcap = (size_t)tier_cap(h, TIER_MAIN);
+    std::map<int, double> growth;   // observed output/input per sub-layer kind
+    auto growth_of = [&](int s) {
+        auto it = growth.find(h->sub_kind[s]);
+        return it == growth.end() ? 3.0 : it->second;
+    };
+    // buckets for sub-layer s holding about n strings: its tile must also hold
+    // the strings the sub-layer creates, so aim at tcap / (1.6 * growth)
+    auto buckets_for = [&](int s, double n) {
+        double per = (double)tcap / (1.6 * std::max(1.0, growth_of(s)));
+        per = std::max(per, 16.0);
+        return pow2_at_least(n / per, h->fill_cap);
+    };
 
     StepParams p;
     std::memset(&p, 0, sizeof(p));
@@ -676,80 +746,109 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     p.w_max = w_max;
     p.counters = h->counters;
     p.delta = h->delta;
-    p.deferred = h->deferred;
+    p.rpx = h->spill_raw.x;
+    p.rpz = h->spill_raw.z;
+    p.rpc = h->spill_raw.c;
+    p.rpb = h->spill_b;
+    p.rps = h->spill_s;
+    p.rpcap = h->spill_cap;
+    p.spx = h->spill_grp.x;
+    p.spz = h->spill_grp.z;
+    p.spc = h->spill_grp.c;
+    p.spcap = h->spill_cap;
 
-    // scatter input into the first sub-layer's buckets
-    p.sx = h->arena[side].x;
-    p.sz = h->arena[side].z;
-    p.sc = h->arena[side].c;
-    p.scap = h->cap;
-    p.sfill = h->fill[side];
-    p.sB = B;
-    p.sC = C;
-    p.desc = h->d_subs;
-    if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, p, &launches));
+    // scatter the input into the first sub-layer's buckets
+    int side = 0;
+    uint32_t B = buckets_for(0, (double)n_terms);
+    uint64_t C = h->cap / B;
     unsigned long long ctr[CTR_COUNT];
+    CK(cudaMemsetAsync(h->fill[side], 0, sizeof(uint32_t) * B, h->st));
+    CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+    p.dx = h->arena[side].x;
+    p.dz = h->arena[side].z;
+    p.dc = h->arena[side].c;
+    p.dcap = h->cap;
+    p.dfill = h->fill[side];
+    p.dB = B;
+    p.dC = C;
+    p.next = h->d_subs;
+    if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, p, &launches));
     CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    if (ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input scatter overflowed a bucket");
+    if (ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input overflowed the overflow area");
+    CK(group_spill(h, side, B, C, ctr[CTR_SPILL], &launches));
+
     size_t N = n_terms;
     size_t peak = N;
     double updates = 0.0;
-
     const int S = (int)h->subs.size();
     for (int s = 0; s < S; ++s) {
         const SubLayerDesc& d = h->subs[s];
         const bool fin = d.final_ != 0;
-        int kind = h->sub_kind[s];
-        double g = growth.count(kind) ? growth[kind] : 3.0;
-        double est = std::max(64.0, (double)N * g * 1.3);
-        uint32_t nB = fin ? 1 : pow2_at_least(est / target, h->fill_cap);
-        int attempt = 0;
-        for (;;) {
-            uint64_t nC = fin ? h->cap : h->cap / nB;
-            if (!fin) CK(cudaMemsetAsync(h->fill[side ^ 1], 0, sizeof(uint32_t) * nB, h->st));
-            CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
-            CK(cudaMemsetAsync(h->delta, 0, sizeof(long long) * MAX_SITES, h->st));
-            p.sx = h->arena[side].x;
-            p.sz = h->arena[side].z;
-            p.sc = h->arena[side].c;
-            p.scap = h->cap;
-            p.sfill = h->fill[side];
-            p.sB = B;
-            p.sC = C;
-            p.dx = h->arena[side ^ 1].x;
-            p.dz = h->arena[side ^ 1].z;
-            p.dc = h->arena[side ^ 1].c;
-            p.dcap = h->cap;
-            p.dfill = h->fill[side ^ 1];
-            p.dB = nB;
-            p.dC = nC;
-            p.desc = h->d_subs + s;
-            p.next = fin ? nullptr : h->d_subs + s + 1;
-            p.has_noise = d.noise >= 0;
-            if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
-            p.max_load = (uint32_t)(tcap / 2);
-            CK(dispatch_process(h, p, false, 0, &launches));
+        const int kind = h->sub_kind[s];
+        double est = std::max(64.0, (double)N * growth_of(s) * 1.3);
+        const uint32_t nB = fin ? 1 : buckets_for(s + 1, est);
+        const uint64_t nC = fin ? h->cap : h->cap / nB;
+        if (!fin) CK(cudaMemsetAsync(h->fill[side ^ 1], 0, sizeof(uint32_t) * nB, h->st));
+        CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+        CK(cudaMemsetAsync(h->delta, 0, sizeof(long long) * MAX_SITES, h->st));
+        p.sx = h->arena[side].x;
+        p.sz = h->arena[side].z;
+        p.sc = h->arena[side].c;
+        p.scap = h->cap;
+        p.sfill = h->fill[side];
+        p.soff = h->soff[side];
+        p.sB = B;
+        p.sC = C;
+        p.dx = h->arena[side ^ 1].x;
+        p.dz = h->arena[side ^ 1].z;
+        p.dc = h->arena[side ^ 1].c;
+        p.dcap = h->cap;
+        p.dfill = h->fill[side ^ 1];
+        p.dB = nB;
+        p.dC = nC;
+        p.desc = h->d_subs + s;
+        p.next = fin ? nullptr : h->d_subs + s + 1;
+        p.has_noise = d.noise >= 0;
+        if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
+        float ms[3] = {0.f, 0.f, 0.f};
+        unsigned long long passed[2] = {0, 0};
+        // three tiers: main shared-memory tile, large shared-memory tile, global tile
+        for (int tier = TIER_MAIN; tier <= TIER_GLOBAL; ++tier) {
+            uint32_t n_items;
+            if (tier == TIER_MAIN) {
+                p.in_list = nullptr;
+                n_items = B;
+            } else {
+                n_items = (uint32_t)passed[tier - 1];
+                if (n_items == 0) break;
+                p.in_list = tier == TIER_LARGE ? h->list_a : h->list_b;
+            }
+            p.n_list = n_items;
+            p.out_list = tier == TIER_MAIN ? h->list_a : (tier == TIER_LARGE ? h->list_b : nullptr);
+            p.work_ctr = CTR_WORK + tier;
+            p.defer_ctr = tier == TIER_MAIN ? CTR_DEFER1 : CTR_DEFER2;
+            p.max_load = (uint32_t)(tier_cap(h, tier) * 3 / 4);
+            CK(cudaEventRecord(scope.ev[2 * tier], h->st));
+            CK(dispatch_process(h, p, tier, n_items, &launches));
+            CK(cudaEventRecord(scope.ev[2 * tier + 1], h->st));
             CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
             CK(cudaStreamSynchronize(h->st));
-            if (ctr[CTR_DEFERRED]) {
-                uint32_t nd = (uint32_t)ctr[CTR_DEFERRED];
-                stats.fallback_buckets += (int)nd;
-                CK(dispatch_process(h, p, true, nd, &launches));
-                CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
-                CK(cudaStreamSynchronize(h->st));
-                if (ctr[CTR_ERR_FALLBACK])
-                    return fail(h, PP_ERR_CAPACITY,
-                                "sub-layer %d: a bucket exceeds the global-memory tile (%d entries)", s,
-                                kFallbackCap);
-            }
-            if (ctr[CTR_ERR_REGION] == 0) break;
-            if (fin || ctr[CTR_OUT] > h->cap || ++attempt > 4)
-                return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed capacity %zu", s,
-                            (unsigned long long)ctr[CTR_OUT], h->cap);
-            // a bucket region overflowed: fewer, larger regions and run the sub-layer again
-            nB = std::max<uint32_t>(1, nB / 4);
+            cudaEventElapsedTime(&ms[tier], scope.ev[2 * tier], scope.ev[2 * tier + 1]);
+            stats.tier_launches[tier]++;
+            stats.tier_ms[tier] += ms[tier];
+            stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];
+            if (tier < TIER_GLOBAL) passed[tier] = ctr[tier == TIER_MAIN ? CTR_DEFER1 : CTR_DEFER2];
         }
+        stats.fallback_buckets += (int)passed[1];
+        if (ctr[CTR_ERR_FALLBACK])
+            return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s,
+                        kFallbackCap);
+        if (ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap)
+            return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
+                        "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap,
+                        h->spill_cap);
+        if (!fin) CK(group_spill(h, side ^ 1, nB, nC, ctr[CTR_SPILL], &launches));
         long long dl[MAX_SITES];
         CK(cudaMemcpyAsync(dl, h->delta, sizeof(dl), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
@@ -759,13 +858,20 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
             updates += live;
             live += (double)dl[j];
         }
-        size_t Nout = (size_t)ctr[CTR_OUT];
+        const size_t Nout = (size_t)ctr[CTR_OUT];
+        if (trace)
+            fprintf(trace,
+                    "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"n_in\": %zu, \"n_out\": %zu, "
+                    "\"buckets_in\": %u, \"buckets_out\": %u, \"to_large\": %llu, \"to_global\": %llu, "
+                    "\"spill\": %llu, \"ms_main\": %.4f, \"ms_large\": %.4f, \"ms_global\": %.4f}\n",
+                    s, d.cls, d.n_gates, N, Nout, B, nB, passed[0], passed[1],
+                    (unsigned long long)ctr[CTR_SPILL], ms[0], ms[1], ms[2]);
         if (N > 0) growth[kind] = std::max(0.05, (double)Nout / (double)N);
         N = Nout;
         peak = std::max(peak, N);
         side ^= 1;
         B = nB;
-        C = fin ? h->cap : h->cap / nB;
+        C = nC;
         stats.n_sublayers++;
     }
     h->res_side = side;
@@ -775,9 +881,9 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     stats.peak_terms = peak;
     stats.updates = updates;
     stats.kernel_launches = launches;
+    stats.bytes_per_string = (double)term_bytes(h);
     stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     h->stats = stats;
-    (void)f32;
     return PP_OK;
 }
 

@@ -10,14 +10,22 @@ namespace pp {
 // Per-launch parameters of one sub-layer.  Term arrays are word-major:
 // x[w * cap + i].  Bucket b of a layout owns indices [b*C, b*C + fill[b]).
 struct StepParams {
+    // source layout (this sub-layer's buckets)
     const uint64_t* sx;
     const uint64_t* sz;
     const void* sc;
     uint64_t scap;
-    const uint32_t* sfill;
+    const uint32_t* sfill;        // strings routed to each bucket (may exceed sC)
     uint32_t sB;
     uint64_t sC;
+    // source overflow: strings beyond a bucket's region, grouped by bucket
+    const uint64_t* spx;
+    const uint64_t* spz;
+    const void* spc;
+    uint64_t spcap;
+    const uint64_t* soff;         // first overflow index of each bucket
 
+    // destination layout (next sub-layer's buckets, or the compact result)
     uint64_t* dx;
     uint64_t* dz;
     void* dc;
@@ -25,6 +33,13 @@ struct StepParams {
     uint32_t* dfill;
     uint32_t dB;
     uint64_t dC;
+    // destination overflow, in arrival order: string, bucket, index past the region
+    uint64_t* rpx;
+    uint64_t* rpz;
+    void* rpc;
+    uint32_t* rpb;
+    uint32_t* rps;
+    uint64_t rpcap;
 
     const SubLayerDesc* desc;
     const SubLayerDesc* next;     // nullptr when desc is final
@@ -36,19 +51,28 @@ struct StepParams {
 
     unsigned long long* counters; // see CTR_* below
     long long* delta;             // [MAX_SITES] net change of live terms by listed gate
-    uint32_t* deferred;           // bucket ids left to the global-memory path
-    uint32_t max_load;            // buckets with more entries are deferred
+    const uint32_t* in_list;      // buckets to process (nullptr: all of 0..sB-1)
+    uint32_t n_list;
+    uint32_t* out_list;           // buckets this tier could not hold (nullptr: report failure)
+    int work_ctr;                 // counter index of this launch's work queue
+    int defer_ctr;                // counter index of out_list's length
+    uint32_t max_load;            // buckets with more strings are passed on
 };
 
 enum {
-    CTR_WORK = 0,        // bucket work queue
-    CTR_OUT = 1,         // terms written (next layout or final)
-    CTR_PROLOGUE = 2,    // live terms after the prologue (merge / noise)
-    CTR_DEFERRED = 3,    // buckets deferred
-    CTR_ERR_REGION = 4,  // writes dropped because a bucket region was full
-    CTR_ERR_FALLBACK = 5,// buckets too large even for the global-memory path
-    CTR_WORK_FB = 6,     // work queue of the fallback kernel
-    CTR_COUNT = 8
+    CTR_WORK = 0,        // work queues, one per tier
+    CTR_WORK2 = 1,
+    CTR_WORK3 = 2,
+    CTR_OUT = 3,         // terms written (next layout or final)
+    CTR_PROLOGUE = 4,    // live terms after the prologue (merge / noise)
+    CTR_DEFER1 = 5,      // buckets passed from the main tier to the large tier
+    CTR_DEFER2 = 6,      // buckets passed from the large tier to the global tier
+    CTR_ERR_REGION = 7,  // strings dropped: overflow area or result full
+    CTR_ERR_FALLBACK = 8,// buckets too large even for the global tier
+    CTR_SPILL = 9,       // strings written to the destination overflow area
+    CTR_LOADED = 12,     // strings loaded by completed buckets, per tier (12..14)
+    CTR_EMITTED = 15,    // strings written by completed buckets, per tier (15..17)
+    CTR_COUNT = 20
 };
 
 // Working set of one bucket.  Arrays live in shared memory (main kernel) or in a
@@ -148,6 +172,37 @@ __device__ __forceinline__ double eps_of<double>(const StepParams& p) { return p
 template <>
 __device__ __forceinline__ float eps_of<float>(const StepParams& p) { return p.eps_f; }
 
+// Appends a string to bucket nb of the destination layout: into the bucket's
+// region while it has room, else into the overflow area.
+template <int W, typename T>
+__device__ __forceinline__ void emit(const StepParams& p, uint32_t nb, const uint64_t* x,
+                                     const uint64_t* z, T c) {
+    uint32_t slot = atomicAdd(&p.dfill[nb], 1u);
+    if ((uint64_t)slot < p.dC) {
+        size_t pos = (size_t)nb * p.dC + slot;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            p.dx[(size_t)w * p.dcap + pos] = x[w];
+            p.dz[(size_t)w * p.dcap + pos] = z[w];
+        }
+        static_cast<T*>(p.dc)[pos] = c;
+        return;
+    }
+    unsigned long long k = atomicAdd(&p.counters[CTR_SPILL], 1ull);
+    if (k < p.rpcap) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            p.rpx[(size_t)w * p.rpcap + k] = x[w];
+            p.rpz[(size_t)w * p.rpcap + k] = z[w];
+        }
+        static_cast<T*>(p.rpc)[k] = c;
+        p.rpb[k] = nb;
+        p.rps[k] = slot - (uint32_t)p.dC;
+    } else {
+        atomicAdd(&p.counters[CTR_ERR_REGION], 1ull);
+    }
+}
+
 // Processes one bucket: load, prologue (merge/truncate the input observable,
 // noise map), gate rounds, then writes the surviving strings into the next
 // layout's buckets (or the compact final array).  Returns false, having
@@ -158,32 +213,37 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
     const SubLayerDesc& d = *p.desc;
     const int tid = threadIdx.x, nt = blockDim.x;
     const T eps = eps_of<T>(p);
-    uint32_t n_in = p.sfill[b];
-    if ((uint64_t)n_in > p.sC) n_in = (uint32_t)p.sC;
+    const uint32_t n_in = p.sfill[b];
 
     for (int i = tid; i < t.hcap; i += nt) t.hash[i] = -1;
     for (int i = tid; i < MAX_SITES; i += nt) s_delta[i] = 0;
     if (tid == 0) {
         *t.n = (int)n_in;
-        *t.flag = (n_in > (uint32_t)(t.cap / 2)) ? 1 : 0;
+        *t.flag = (n_in > p.max_load) ? 1 : 0;
         *t.kmax = 0;
         *t.live = 0;
     }
     __syncthreads();
     if (*t.flag) return false;
 
-    // ---- load
+    // ---- load: the bucket's region, then its overflow strings
     const size_t base = (size_t)b * p.sC;
+    const size_t obase = (n_in > p.sC) ? (size_t)p.soff[b] : 0;
     for (int i = tid; i < (int)n_in; i += nt) {
         uint64_t x[W], z[W];
+        const bool reg = (uint64_t)i < p.sC;
+        const size_t src = reg ? base + i : obase + (i - p.sC);
+        const uint64_t* ax = reg ? p.sx : p.spx;
+        const uint64_t* az = reg ? p.sz : p.spz;
+        const size_t acap = reg ? p.scap : p.spcap;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            x[w] = p.sx[(size_t)w * p.scap + base + i];
-            z[w] = p.sz[(size_t)w * p.scap + base + i];
+            x[w] = ax[(size_t)w * acap + src];
+            z[w] = az[(size_t)w * acap + src];
             t.x[(size_t)w * t.cap + i] = x[w];
             t.z[(size_t)w * t.cap + i] = z[w];
         }
-        t.c[i] = load_coef<W, T>(p.sc, base + i);
+        t.c[i] = load_coef<W, T>(reg ? p.sc : p.spc, src);
         t.rv[i] = 0;
         if (d.first) __threadfence_block();
         tile_insert<W, T>(t, i, x, z, d.first != 0);
@@ -329,7 +389,10 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
             if (t.c[i] != T(0)) ++cnt;
         int off = cnt ? atomicAdd(t.live, cnt) : 0;
         __syncthreads();
-        if (tid == 0) s_base = atomicAdd(&p.counters[CTR_OUT], (unsigned long long)*t.live);
+        if (tid == 0) {
+            s_base = atomicAdd(&p.counters[CTR_OUT], (unsigned long long)*t.live);
+            atomicAdd(&p.counters[CTR_EMITTED + (p.work_ctr - CTR_WORK)], (unsigned long long)*t.live);
+        }
         __syncthreads();
         unsigned long long pos = s_base + off;
         for (int i = tid; i < nf; i += nt) {
@@ -359,23 +422,18 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
             uint64_t x[W], z[W];
             tile_key<W, T>(t, i, x, z);
             uint32_t nb = bucket_of<W>(dn, x, z, bmask);
-            uint32_t slot = atomicAdd(&p.dfill[nb], 1u);
-            if ((uint64_t)slot < p.dC) {
-                size_t pos = (size_t)nb * p.dC + slot;
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    p.dx[(size_t)w * p.dcap + pos] = x[w];
-                    p.dz[(size_t)w * p.dcap + pos] = z[w];
-                }
-                static_cast<T*>(p.dc)[pos] = c;
-            } else {
-                atomicAdd(&p.counters[CTR_ERR_REGION], 1ull);
-            }
+            emit<W, T>(p, nb, x, z, c);
         }
-        if (cnt) atomicAdd(&p.counters[CTR_OUT], (unsigned long long)cnt);
+        if (cnt) {
+            atomicAdd(&p.counters[CTR_OUT], (unsigned long long)cnt);
+            atomicAdd(&p.counters[CTR_EMITTED + (p.work_ctr - CTR_WORK)], (unsigned long long)cnt);
+        }
     }
     __syncthreads();
-    if (tid == 0) atomicAdd(&p.counters[CTR_PROLOGUE], (unsigned long long)live0);
+    if (tid == 0) {
+        atomicAdd(&p.counters[CTR_PROLOGUE], (unsigned long long)live0);
+        atomicAdd(&p.counters[CTR_LOADED + (p.work_ctr - CTR_WORK)], (unsigned long long)n_in);
+    }
     for (int i = tid; i < MAX_SITES; i += nt)
         if (s_delta[i])
             atomicAdd(reinterpret_cast<unsigned long long*>(&p.delta[i]),
@@ -411,8 +469,9 @@ __device__ __forceinline__ Tile<W, T> carve_tile(unsigned char* mem, int cap, in
     return t;
 }
 
-// Main path: persistent CTAs take buckets from a work queue; the tile lives in
-// dynamic shared memory.
+// Shared-memory tiers: persistent CTAs take buckets from a work queue (all
+// buckets, or the list a smaller tier passed on); a bucket that does not fit is
+// passed to the next tier.
 template <int W, typename T>
 __global__ void k_process(StepParams p, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -420,47 +479,54 @@ __global__ void k_process(StepParams p, int cap) {
     __shared__ int s_delta[MAX_SITES];
     __shared__ uint32_t s_b;
     Tile<W, T> t = carve_tile<W, T>(smem, cap, ctl);
+    const uint32_t n_items = p.in_list ? p.n_list : p.sB;
     for (;;) {
-        if (threadIdx.x == 0) s_b = (uint32_t)atomicAdd(&p.counters[CTR_WORK], 1ull);
+        if (threadIdx.x == 0) s_b = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);
         __syncthreads();
-        const uint32_t b = s_b;
-        if (b >= p.sB) break;
+        const uint32_t k = s_b;
+        if (k >= n_items) break;
+        const uint32_t b = p.in_list ? p.in_list[k] : k;
         if (p.sfill[b] != 0) {
             bool ok = process_bucket<W, T>(t, p, b, s_delta);
             if (!ok && threadIdx.x == 0) {
-                unsigned long long k = atomicAdd(&p.counters[CTR_DEFERRED], 1ull);
-                p.deferred[k] = b;
+                if (p.out_list) {
+                    unsigned long long j = atomicAdd(&p.counters[p.defer_ctr], 1ull);
+                    p.out_list[j] = b;
+                } else {
+                    atomicAdd(&p.counters[CTR_ERR_FALLBACK], 1ull);
+                }
             }
         }
         __syncthreads();
     }
 }
 
-// Fallback path for deferred buckets: same processor, tile in a global scratch slice.
+// Global tier for the largest buckets: the same processor with the tile in a
+// per-CTA slice of global scratch memory.
 template <int W, typename T>
-__global__ void k_process_global(StepParams p, unsigned char* scratch, size_t slice_bytes, int cap,
-                                 uint32_t n_deferred) {
+__global__ void k_process_global(StepParams p, unsigned char* scratch, size_t slice_bytes, int cap) {
     __shared__ int ctl[4];
     __shared__ int s_delta[MAX_SITES];
     __shared__ uint32_t s_k;
     Tile<W, T> t = carve_tile<W, T>(scratch + slice_bytes * blockIdx.x, cap, ctl);
     for (;;) {
-        if (threadIdx.x == 0) s_k = (uint32_t)atomicAdd(&p.counters[CTR_WORK_FB], 1ull);
+        if (threadIdx.x == 0) s_k = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);
         __syncthreads();
         const uint32_t k = s_k;
-        if (k >= n_deferred) break;
-        bool ok = process_bucket<W, T>(t, p, p.deferred[k], s_delta);
+        if (k >= p.n_list) break;
+        bool ok = process_bucket<W, T>(t, p, p.in_list[k], s_delta);
         if (!ok && threadIdx.x == 0) atomicAdd(&p.counters[CTR_ERR_FALLBACK], 1ull);
         __syncthreads();
     }
 }
 
-// Scatters the input observable into the first sub-layer's buckets.
+// Scatters the input observable into the first sub-layer's buckets (the
+// destination layout of p).
 template <int W, typename T>
 __global__ void k_scatter_input(const uint64_t* ox, const uint64_t* oz, const double* oc, size_t n,
                                 StepParams p) {
-    const SubLayerDesc& d = *p.desc;
-    const uint32_t bmask = p.sB - 1;
+    const SubLayerDesc& d = *p.next;
+    const uint32_t bmask = p.dB - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         uint64_t x[W], z[W];
@@ -470,18 +536,46 @@ __global__ void k_scatter_input(const uint64_t* ox, const uint64_t* oz, const do
             z[w] = oz[i * W + w];
         }
         uint32_t b = bucket_of<W>(d, x, z, bmask);
-        uint32_t slot = atomicAdd(const_cast<uint32_t*>(p.sfill) + b, 1u);
-        if ((uint64_t)slot < p.sC) {
-            size_t pos = (size_t)b * p.sC + slot;
+        emit<W, T>(p, b, x, z, T(oc[i]));
+    }
+}
+
+// Overflow bookkeeping: each bucket whose count exceeds its region gets a
+// contiguous range of the grouped overflow area.
+__global__ void k_spill_offsets(const uint32_t* fill, uint32_t nB, uint64_t C, uint64_t* soff,
+                                unsigned long long* total) {
+    __shared__ unsigned long long s_scan[1024];
+    __shared__ unsigned long long s_base;
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long ex = 0;
+    if (b < nB && (uint64_t)fill[b] > C) ex = (uint64_t)fill[b] - C;
+    s_scan[threadIdx.x] = ex;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        unsigned long long v = (int)threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        s_scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    if (threadIdx.x == blockDim.x - 1) s_base = atomicAdd(total, s_scan[threadIdx.x]);
+    __syncthreads();
+    if (b < nB) soff[b] = s_base + s_scan[threadIdx.x] - ex;
+}
+
+template <int W, typename T>
+__global__ void k_spill_move(const uint64_t* rx, const uint64_t* rz, const T* rc, const uint32_t* rb,
+                             const uint32_t* rs, uint64_t rcap, uint64_t n, const uint64_t* soff,
+                             uint64_t* ox, uint64_t* oz, T* oc, uint64_t ocap) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t dst = soff[rb[k]] + rs[k];
+        if (dst >= ocap) continue;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const_cast<uint64_t*>(p.sx)[(size_t)w * p.scap + pos] = x[w];
-                const_cast<uint64_t*>(p.sz)[(size_t)w * p.scap + pos] = z[w];
-            }
-            static_cast<T*>(const_cast<void*>(p.sc))[pos] = T(oc[i]);
-        } else {
-            atomicAdd(&p.counters[CTR_ERR_REGION], 1ull);
+        for (int w = 0; w < W; ++w) {
+            ox[(size_t)w * ocap + dst] = rx[(size_t)w * rcap + k];
+            oz[(size_t)w * ocap + dst] = rz[(size_t)w * rcap + k];
         }
+        oc[dst] = rc[k];
     }
 }
 

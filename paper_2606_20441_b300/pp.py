@@ -47,7 +47,11 @@ class pp_stats(ctypes.Structure):
                 ("n_sublayers", ctypes.c_int),
                 ("kernel_launches", ctypes.c_int),
                 ("fallback_buckets", ctypes.c_int),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double),
+                ("tier_launches", ctypes.c_int * 3),
+                ("tier_ms", ctypes.c_double * 3),
+                ("tier_strings", ctypes.c_double * 3),
+                ("bytes_per_string", ctypes.c_double)]
 
 
 class PPError(RuntimeError):
