@@ -138,12 +138,12 @@ typedef struct {
     int kernel_launches;     /* kernels this library launched in the last propagation  */
     int fallback_buckets;    /* buckets processed by the global-memory path            */
     double seconds;          /* wall time of the last pp_propagate (host clock)        */
-    /* per processing tier (0: main shared-memory tile, 1: large shared-memory tile,
-       2: global-memory tile): launches, summed device time from CUDA events on the
-       handle's stream, and strings read + written by completed buckets */
-    int tier_launches[3];
-    double tier_ms[3];
-    double tier_strings[3];
+    /* per processing tier (0..2: shared-memory tiles of growing size, 3: global-memory
+       tile): launches, summed device time from CUDA events on the handle's stream, and
+       strings read + written by completed buckets */
+    int tier_launches[4];
+    double tier_ms[4];
+    double tier_strings[4];
     double bytes_per_string;  /* bytes of one stored string (x, z words and coefficient) */
 } pp_stats;
 

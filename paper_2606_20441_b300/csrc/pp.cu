@@ -13,35 +13,53 @@
 
 #include "pp.h"
 #include "pp_kernels.cuh"
+#include "pp_warp.cuh"
 
 using namespace pp;
 
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kTileCap1 = 2048;   // main shared-memory tile entries, W = 1
-constexpr int kTileCap2 = 1024;   // W = 2
-constexpr int kBigCap1 = 4096;    // large shared-memory tier (one CTA per SM)
-constexpr int kBigCap2 = 2048;
-constexpr int kFallbackCTAs = 32; // global-memory tier
+// Processing tiers: a bucket goes to the first tier whose tile holds it.  Small
+// CTAs first, many per SM, so that one CTA's per-round barriers overlap other
+// CTAs' work; then larger shared-memory tiles; then a global-memory tile.
+struct TierCfg {
+    int threads;
+    int cap1;     // tile entries for W = 1
+    int cap2;     // tile entries for W = 2
+};
+constexpr TierCfg kTiers[N_TIERS] = {
+    {32 * WARP_TILE_WARPS, 248, 248},   // one warp per bucket
+    {512, 1024, 1024},                  // CTA tiles
+    {1024, 4096, 2048},
+    {512, 1 << 20, 1 << 20}};           // global-memory tile
+constexpr int kGlobalTier = N_TIERS - 1;
+constexpr int kFallbackCTAs = 16; // CTAs of the global tier
 constexpr int kFallbackCap = 1 << 20;
 
 struct NoiseHost {
     int mode = 0;
-    std::vector<int64_t> t1;          // [n][4]
-    std::vector<int32_t> pair_off, pair_other, pair_id;
-    std::vector<int64_t> t2;          // [P][16]
+    std::vector<int64_t> t1;          // [n][4]  per-site sums incl. one-sided pair parts
+    std::vector<int32_t> shift;       // [n_shift]
+    std::vector<uint64_t> smask;      // [n_shift][W]
+    std::vector<int32_t> pidx;        // [n_shift][n]
+    std::vector<int64_t> c2;          // [P][16]
     std::vector<uint64_t> gx, gz;
     std::vector<int64_t> glam;
+    std::vector<double> etab;         // [8][256] exp(+-2 b 2^(8i-56))
     // device copies
+    double* d_etab = nullptr;
     int64_t* d_t1 = nullptr;
-    int32_t* d_pair_off = nullptr;
-    int32_t* d_pair_other = nullptr;
-    int32_t* d_pair_id = nullptr;
-    int64_t* d_t2 = nullptr;
+    int32_t* d_shift = nullptr;
+    uint64_t* d_smask = nullptr;
+    int32_t* d_pidx = nullptr;
+    int64_t* d_c2 = nullptr;
     uint64_t* d_gx = nullptr;
     uint64_t* d_gz = nullptr;
     int64_t* d_glam = nullptr;
+    std::vector<void*> device_ptrs() const {
+        return {(void*)d_t1, (void*)d_shift, (void*)d_smask, (void*)d_pidx, (void*)d_c2,
+                (void*)d_gx, (void*)d_gz, (void*)d_glam, (void*)d_etab};
+    }
 };
 
 struct Arena {
@@ -78,12 +96,12 @@ struct pp_handle {
     uint32_t fill_cap = 0;
     unsigned long long* counters = nullptr;
     long long* delta = nullptr;
-    uint32_t* list_a = nullptr;    // buckets passed main -> large tier
-    uint32_t* list_b = nullptr;    // buckets passed large -> global tier
+    uint32_t* pass_list[N_TIERS - 1] = {nullptr, nullptr, nullptr};   // buckets passed tier t -> t+1
     size_t spill_cap = 0;          // overflow strings per layout
     Arena spill_raw, spill_grp;
     uint32_t* spill_b = nullptr;
     uint32_t* spill_s = nullptr;
+    unsigned long long* spill_ctr = nullptr;   // [NSPILL]
     uint64_t* soff[2] = {nullptr, nullptr};
     unsigned char* fb_scratch = nullptr;
     size_t fb_slice = 0;
@@ -203,9 +221,19 @@ int sig_kind(const SubLayerDesc& d) {
     return d.cls;
 }
 
+// Gates fused into one sub-layer.  An orbit of a sub-layer can hold up to
+// 2^(acting gates) strings, so smaller sub-layers keep orbits small enough for
+// the one-warp tiles at the price of more passes over the strings.
+int max_fused_gates(const pp_handle* h) {
+    int m = std::min(16, 64 * h->W);   // measured best trade-off on the 6x6 and 7x8 TFIM workloads
+    if (const char* e = getenv("PP_MAX_FUSED_GATES")) m = std::max(1, std::min(m, atoi(e)));
+    return m;
+}
+
 // Splits a layer's gates (listed order) into fused sub-layers.
 void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int layer) {
     const int W = h->W, n = h->n;
+    const int max_gates = max_fused_gates(h);
     std::vector<SubLayerDesc> out;
     SubLayerDesc cur;
     bool open = false;
@@ -234,7 +262,7 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
         double cs, sn;
         trig(h->theta[g], &cs, &sn);
         if (s.cls == CLS_GENERIC) {
-            if (!(open && cur.cls == CLS_GENERIC && cur.n_gates < MAX_GEN)) {
+            if (!(open && cur.cls == CLS_GENERIC && cur.n_gates < std::min(MAX_GEN, max_gates))) {
                 close();
                 start(s);
             }
@@ -246,10 +274,11 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
             cur.cs[j] = cs;
             cur.sn[j] = sn;
             cur.order[j] = (int16_t)j;
+            cur.slot_of[j] = (int16_t)j;
             continue;
         }
         bool fits = open && cur.cls != CLS_GENERIC && cur_sig.same(s) && !used[s.slot] &&
-                    (s.slot > last_slot || cur.nseg < MAX_SEG);
+                    (s.slot > last_slot || cur.nseg < MAX_SEG) && cur.n_gates < max_gates;
         if (!fits) {
             close();
             start(s);
@@ -261,6 +290,7 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
         cur.cs[s.slot] = cs;
         cur.sn[s.slot] = sn;
         cur.order[s.slot] = (int16_t)cur.n_gates;
+        cur.slot_of[cur.n_gates] = (int16_t)s.slot;
         cur.n_gates++;
         used[s.slot] = true;
         last_slot = s.slot;
@@ -313,19 +343,16 @@ size_t term_bytes(const pp_handle* h) {
     return 2 * (size_t)h->W * 8 + (h->opt.precision == PP_PRECISION_FP32 ? 4 : 8);
 }
 
-int tile_cap(const pp_handle* h) { return h->W == 1 ? kTileCap1 : kTileCap2; }
+int tile_cap(const pp_handle* h) { return h->W == 1 ? kTiers[0].cap1 : kTiers[0].cap2; }
 
-size_t tile_smem(const pp_handle* h) {
-    size_t per = h->opt.precision == PP_PRECISION_FP32
-                     ? (h->W == 1 ? tile_bytes_per_entry<1, float>() : tile_bytes_per_entry<2, float>())
-                     : (h->W == 1 ? tile_bytes_per_entry<1, double>() : tile_bytes_per_entry<2, double>());
-    return per * (size_t)tile_cap(h);
-}
-
-size_t tile_entry_bytes(const pp_handle* h) {
-    return h->opt.precision == PP_PRECISION_FP32
-               ? (h->W == 1 ? tile_bytes_per_entry<1, float>() : tile_bytes_per_entry<2, float>())
-               : (h->W == 1 ? tile_bytes_per_entry<1, double>() : tile_bytes_per_entry<2, double>());
+// Bytes of one global-tier slice (int32 indices).
+size_t global_slice_bytes(const pp_handle* h) {
+    size_t carved = h->opt.precision == PP_PRECISION_FP32
+        ? (h->W == 1 ? tile_layout_bytes<1, float, int32_t>(kFallbackCap)
+                     : tile_layout_bytes<2, float, int32_t>(kFallbackCap))
+        : (h->W == 1 ? tile_layout_bytes<1, double, int32_t>(kFallbackCap)
+                     : tile_layout_bytes<2, double, int32_t>(kFallbackCap));
+    return (carved + 255) & ~(size_t)255;
 }
 
 pp_status alloc_arena(pp_handle* h, Arena* a, size_t cap) {
@@ -351,11 +378,13 @@ pp_status ensure_memory(pp_handle* h) {
     pp_status st;
     for (int s = 0; s < 2; ++s)
         if ((st = alloc_arena(h, &h->arena[s], cap)) != PP_OK) return st;
-    h->spill_cap = std::max<size_t>(cap / 4, 4096);
+    h->spill_cap = std::max<size_t>(cap / 4, 4096) / NSPILL * NSPILL;
     if ((st = alloc_arena(h, &h->spill_raw, h->spill_cap)) != PP_OK) return st;
     if ((st = alloc_arena(h, &h->spill_grp, h->spill_cap)) != PP_OK) return st;
     h->spill_b = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
     h->spill_s = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
+    h->spill_ctr = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * NSPILL));
+    if (!h->spill_ctr) return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     h->fill_cap = (uint32_t)std::min<size_t>(std::max<size_t>(cap / 64, 1024), 1u << 28);
     for (int s = 0; s < 2; ++s) {
         h->fill[s] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
@@ -364,53 +393,77 @@ pp_status ensure_memory(pp_handle* h) {
     }
     h->counters = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * CTR_COUNT));
     h->delta = static_cast<long long*>(dev_alloc(h, sizeof(long long) * MAX_SITES));
-    h->list_a = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
-    h->list_b = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
+    for (int k = 0; k < N_TIERS - 1; ++k)
+        if (!(h->pass_list[k] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap))))
+            return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * 4096));
-    h->fb_slice = (tile_entry_bytes(h) * kFallbackCap + 255) & ~(size_t)255;
+    h->fb_slice = global_slice_bytes(h);
+    if (h->fb_slice == 0) return fail(h, PP_ERR_CUDA, "internal: global tile layout exceeds its slice");
     h->fb_scratch = static_cast<unsigned char*>(dev_alloc(h, h->fb_slice * kFallbackCTAs));
-    if (!h->spill_b || !h->spill_s || !h->counters || !h->delta || !h->list_a || !h->list_b ||
+    if (!h->spill_b || !h->spill_s || !h->counters || !h->delta ||
         !h->partial || !h->fb_scratch)
         return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     return PP_OK;
 }
 
+// Smallest power of two >= v, but at most the largest power of two <= cap.
 uint32_t pow2_at_least(double v, uint32_t cap) {
     uint32_t b = 1;
-    while ((double)b < v && b < cap) b <<= 1;
+    while ((double)b < v && 2ull * b <= cap) b <<= 1;
     return b;
 }
 
-enum Tier { TIER_MAIN = 0, TIER_LARGE = 1, TIER_GLOBAL = 2 };
-
-template <int W, typename T>
-cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t n_items, int* launches) {
-    if (tier == TIER_GLOBAL) {
-        uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)kFallbackCTAs);
-        k_process_global<W, T><<<grid, kThreads, 0, h->st>>>(p, h->fb_scratch, h->fb_slice, kFallbackCap);
-    } else {
-        int cap = tier == TIER_MAIN ? (W == 1 ? kTileCap1 : kTileCap2) : (W == 1 ? kBigCap1 : kBigCap2);
-        size_t smem = tile_bytes_per_entry<W, T>() * (size_t)cap;
-        static int attr_set = 0;
-        if (attr_set < (int)smem) {
-            cudaFuncSetAttribute(k_process<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set = (int)smem;
-        }
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T>, kThreads, smem);
-        per_sm = std::max(per_sm, 1);
-        uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(per_sm * h->sm_count));
-        k_process<W, T><<<grid, kThreads, smem, h->st>>>(p, cap);
+template <int W, typename T, int NT>
+cudaError_t launch_smem_tier(pp_handle* h, const StepParams& p, int cap, uint32_t n_items) {
+    const size_t smem = tile_layout_bytes<W, T, int16_t>((size_t)cap);
+    static size_t attr_set = 0;
+    if (attr_set < smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_process<W, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = smem;
     }
-    ++*launches;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T, NT>, NT, smem);
+    per_sm = std::max(per_sm, 1);
+    uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(per_sm * h->sm_count));
+    k_process<W, T, NT><<<grid, NT, smem, h->st>>>(p, cap);
     return cudaGetLastError();
 }
 
-int tier_cap(const pp_handle* h, int tier) {
-    if (tier == TIER_MAIN) return h->W == 1 ? kTileCap1 : kTileCap2;
-    if (tier == TIER_LARGE) return h->W == 1 ? kBigCap1 : kBigCap2;
-    return kFallbackCap;
+template <int W, typename T>
+cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t n_items, int* launches) {
+    ++*launches;
+    const int cap = W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2;
+    switch (tier) {
+        case 0: {
+            const size_t smem = warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS;
+            static size_t attr_set = 0;
+            if (attr_set < smem) {
+                cudaError_t e = cudaFuncSetAttribute(k_process_warp<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                attr_set = smem;
+            }
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process_warp<W, T>, kTiers[0].threads, smem);
+            per_sm = std::max(per_sm, 1);
+            uint32_t grid = std::min<uint32_t>(std::max<uint32_t>((n_items + WARP_TILE_WARPS - 1) / WARP_TILE_WARPS, 1),
+                                               (uint32_t)(per_sm * h->sm_count));
+            k_process_warp<W, T><<<grid, kTiers[0].threads, smem, h->st>>>(p, cap);
+            return cudaGetLastError();
+        }
+        case 1: return launch_smem_tier<W, T, kTiers[1].threads>(h, p, cap, n_items);
+        case 2: return launch_smem_tier<W, T, kTiers[2].threads>(h, p, cap, n_items);
+        default: {
+            uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)kFallbackCTAs);
+            k_process_global<W, T><<<grid, kTiers[kGlobalTier].threads, 0, h->st>>>(p, h->fb_scratch, h->fb_slice,
+                                                                                  kFallbackCap);
+            return cudaGetLastError();
+        }
+    }
 }
+
+int tier_cap(const pp_handle* h, int tier) { return h->W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2; }
 
 cudaError_t dispatch_process(pp_handle* h, const StepParams& p, int tier, uint32_t n_items, int* launches) {
     bool f32 = h->opt.precision == PP_PRECISION_FP32;
@@ -436,42 +489,83 @@ cudaError_t dispatch_scatter(pp_handle* h, const uint64_t* ox, const uint64_t* o
     return cudaGetLastError();
 }
 
-// Groups the overflow strings of a freshly written layout by bucket.
-cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, uint64_t n_spill, int* launches) {
-    if (n_spill == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(h->counters + CTR_COUNT - 1, 0, sizeof(unsigned long long), h->st);
-    if (e != cudaSuccess) return e;
-    uint32_t grid = (nB + 1023) / 1024;
-    k_spill_offsets<<<grid, 1024, 0, h->st>>>(h->fill[side], nB, C, h->soff[side], h->counters + CTR_COUNT - 1);
-    int g2 = (int)std::min<uint64_t>((n_spill + 255) / 256, 8192);
-    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
-    const Arena& r = h->spill_raw;
-    const Arena& o = h->spill_grp;
-    if (h->W == 1) {
-        if (f32) k_spill_move<1, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
-        else k_spill_move<1, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
-    } else {
-        if (f32) k_spill_move<2, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
-        else k_spill_move<2, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, n_spill, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
-    }
-    *launches += 2;
-    return cudaGetLastError();
-}
-
 NoiseDesc noise_desc(const NoiseHost& nh) {
     NoiseDesc d;
     d.mode = nh.mode;
     d.n_generic = (int)nh.glam.size();
     d.t1 = nh.d_t1;
-    d.pair_off = nh.d_pair_off;
-    d.pair_other = nh.d_pair_other;
-    d.pair_id = nh.d_pair_id;
-    d.t2 = nh.d_t2;
+    d.n_shift = (int)nh.shift.size();
+    d.n_sites = (int)(nh.t1.size() / 4);
+    d.shift = nh.d_shift;
+    d.smask = nh.d_smask;
+    d.pidx = nh.d_pidx;
+    d.c2 = nh.d_c2;
+    d.etab = nh.d_etab;
     d.gen_x = nh.d_gx;
     d.gen_z = nh.d_gz;
     d.gen_lam = nh.d_glam;
     return d;
 }
+
+// Applies noise map nh in place to layout `side` (B buckets of C, plus n_over
+// grouped overflow strings).
+cudaError_t apply_noise(pp_handle* h, const NoiseHost& nh, int side, uint32_t B, uint64_t C, uint64_t n_over,
+                        double eps, float eps_f, int* launches) {
+    NoiseDesc nz = noise_desc(nh);
+    const int n_pairs = (int)(nh.c2.size() / 16);
+    const NoiseSmem L = noise_smem_layout(nz.n_sites, nz.n_shift, n_pairs, h->W);
+    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    const Arena& a = h->arena[side];
+    const Arena& o = h->spill_grp;
+    const int grid = h->sm_count * 4;
+    cudaError_t e;
+#define PP_NOISE_LAUNCH(WW, TT)                                                                         \
+    e = cudaFuncSetAttribute(k_noise<WW, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes); \
+    if (e != cudaSuccess) return e;                                                                     \
+    k_noise<WW, TT><<<grid, 256, L.bytes, h->st>>>(a.x, a.z, (TT*)a.c, h->cap, h->fill[side], B, C, o.x, o.z, \
+                                                 (TT*)o.c, h->spill_cap, n_over, nz, n_pairs, eps, eps_f)
+    if (h->W == 1) {
+        if (f32) { PP_NOISE_LAUNCH(1, float); } else { PP_NOISE_LAUNCH(1, double); }
+    } else {
+        if (f32) { PP_NOISE_LAUNCH(2, float); } else { PP_NOISE_LAUNCH(2, double); }
+    }
+#undef PP_NOISE_LAUNCH
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// Strings in the overflow area after a launch (sum over its shards).
+cudaError_t spill_total(pp_handle* h, unsigned long long* total) {
+    unsigned long long f[NSPILL];
+    cudaError_t e = cudaMemcpyAsync(f, h->spill_ctr, sizeof(f), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    *total = 0;
+    for (int i = 0; i < NSPILL; ++i) *total += f[i];
+    return e;
+}
+
+// Groups the overflow strings of a freshly written layout by bucket.
+cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, uint64_t n_spill, int* launches) {
+    if (n_spill == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(h->counters + CTR_SPILL_TOTAL, 0, sizeof(unsigned long long), h->st);
+    if (e != cudaSuccess) return e;
+    uint32_t grid = (nB + 1023) / 1024;
+    k_spill_offsets<<<grid, 1024, 0, h->st>>>(h->fill[side], nB, C, h->soff[side], h->counters + CTR_SPILL_TOTAL);
+    int g2 = (int)std::min<uint64_t>((h->spill_cap + 255) / 256, 16384);
+    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    const Arena& r = h->spill_raw;
+    const Arena& o = h->spill_grp;
+    if (h->W == 1) {
+        if (f32) k_spill_move<1, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
+        else k_spill_move<1, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
+    } else {
+        if (f32) k_spill_move<2, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
+        else k_spill_move<2, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
+    }
+    *launches += 2;
+    return cudaGetLastError();
+}
+
 
 float eps_float_ceil(double eps) {
     float f = (float)eps;
@@ -564,9 +658,7 @@ pp_status pp_load_circuit(pp_handle* h, size_t n_gates, const uint64_t* rx, cons
     h->n_layers = n_layers;
     for (auto& kv : h->noise) {
         NoiseHost& nh = kv.second;
-        for (void* p : {(void*)nh.d_t1, (void*)nh.d_pair_off, (void*)nh.d_pair_other, (void*)nh.d_pair_id,
-                        (void*)nh.d_t2, (void*)nh.d_gx, (void*)nh.d_gz, (void*)nh.d_glam})
-            dev_free(h, p);
+        for (void* p : nh.device_ptrs()) dev_free(h, p);
     }
     h->noise.clear();
     h->have_circuit = true;
@@ -589,6 +681,7 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
     nh.t1.assign((size_t)n * 4, 0);
     std::map<std::pair<int, int>, int> pid;
     std::vector<std::pair<int, int>> pairs;
+    std::vector<int64_t> t2;            // [P][16] sum over 2-local generators on the pair
     double total = 0.0;
     // anticommutation of single-qubit letters (code x + 2z) by the symplectic form
     auto anti1 = [](int l, int e) { return ((l & 1) & (e >> 1)) ^ ((l >> 1) & (e & 1)); };
@@ -621,14 +714,14 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
                 id = (int)pairs.size();
                 pid[key] = id;
                 pairs.push_back(key);
-                nh.t2.resize(nh.t2.size() + 16, 0);
+                t2.resize(t2.size() + 16, 0);
             } else {
                 id = it->second;
             }
             int ea = bit(x, a) + 2 * bit(z, a), eb = bit(x, b) + 2 * bit(z, b);
             for (int la = 0; la < 4; ++la)
                 for (int lb = 0; lb < 4; ++lb)
-                    if (anti1(la, ea) ^ anti1(lb, eb)) nh.t2[16 * id + la + 4 * lb] += lf;
+                    if (anti1(la, ea) ^ anti1(lb, eb)) t2[16 * id + la + 4 * lb] += lf;
         } else if (sites.size() > 2) {
             nh.gx.insert(nh.gx.end(), x, x + W);
             nh.gz.insert(nh.gz.end(), z, z + W);
@@ -636,40 +729,62 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
         }
     }
     if (total >= 60.0) return fail(h, PP_ERR_ARG, "sum of rates %.3g too large (must be < 60)", total);
-    nh.pair_off.assign(n + 1, 0);
-    for (auto& pr : pairs) {
-        nh.pair_off[pr.first + 1]++;
-        nh.pair_off[pr.second + 1]++;
-    }
-    for (int q = 0; q < n; ++q) nh.pair_off[q + 1] += nh.pair_off[q];
-    nh.pair_other.assign(2 * pairs.size(), 0);
-    nh.pair_id.assign(2 * pairs.size(), 0);
-    std::vector<int> pos(nh.pair_off.begin(), nh.pair_off.end() - 1);
+    // Fold each pair's one-sided terms (the other site carries I) into the
+    // per-site table; keep, per pair, the correction for strings that hold a
+    // non-identity letter on both sites:
+    //   T2[la,lb] = T2[la,I] + T2[I,lb] + C[la,lb]   (exact integers).
+    nh.c2.assign(16 * pairs.size(), 0);
+    std::map<int, int> shift_class;
     for (size_t i = 0; i < pairs.size(); ++i) {
-        int a = pairs[i].first, b = pairs[i].second;
-        nh.pair_other[pos[a]] = b;
-        nh.pair_id[pos[a]++] = (int)i;
-        nh.pair_other[pos[b]] = a;
-        nh.pair_id[pos[b]++] = (int)i;
+        const int a = pairs[i].first, b = pairs[i].second;
+        const int64_t* T = &t2[16 * i];
+        for (int l = 1; l < 4; ++l) {
+            nh.t1[4 * a + l] += T[l];          // (l, I)
+            nh.t1[4 * b + l] += T[4 * l];      // (I, l)
+        }
+        for (int la = 1; la < 4; ++la)
+            for (int lb = 1; lb < 4; ++lb)
+                nh.c2[16 * i + la + 4 * lb] = T[la + 4 * lb] - T[la] - T[4 * lb];
+        const int d = b - a;
+        auto it = shift_class.find(d);
+        int c;
+        if (it == shift_class.end()) {
+            c = (int)nh.shift.size();
+            shift_class[d] = c;
+            nh.shift.push_back(d);
+            nh.smask.resize(nh.smask.size() + W, 0);
+            nh.pidx.resize(nh.pidx.size() + n, -1);
+        } else {
+            c = it->second;
+        }
+        nh.smask[(size_t)c * W + (a >> 6)] |= 1ull << (a & 63);
+        nh.pidx[(size_t)c * n + a] = (int32_t)i;
     }
     auto old = h->noise.find(layer);
     if (old != h->noise.end()) {
         NoiseHost& o = old->second;
-        for (void* p : {(void*)o.d_t1, (void*)o.d_pair_off, (void*)o.d_pair_other, (void*)o.d_pair_id,
-                        (void*)o.d_t2, (void*)o.d_gx, (void*)o.d_gz, (void*)o.d_glam})
-            dev_free(h, p);
+        for (void* p : o.device_ptrs()) dev_free(h, p);
         h->noise.erase(old);
     }
     nh.d_t1 = alloc_copy<int64_t>(h, nh.t1);
-    nh.d_pair_off = alloc_copy<int32_t>(h, nh.pair_off);
-    nh.d_pair_other = alloc_copy<int32_t>(h, nh.pair_other);
-    nh.d_pair_id = alloc_copy<int32_t>(h, nh.pair_id);
-    nh.d_t2 = alloc_copy<int64_t>(h, nh.t2);
+    nh.d_shift = alloc_copy<int32_t>(h, nh.shift);
+    nh.d_smask = alloc_copy<uint64_t>(h, nh.smask);
+    nh.d_pidx = alloc_copy<int32_t>(h, nh.pidx);
+    nh.d_c2 = alloc_copy<int64_t>(h, nh.c2);
+    // factor tables: entry (i, b) = exp(+-2 * b * 2^(8i - 56)), evaluated in extended
+    // precision and rounded once to double
+    nh.etab.assign(8 * 256, 1.0);
+    for (int i = 0; i < 8; ++i)
+        for (int b = 1; b < 256; ++b) {
+            long double e = std::ldexp((long double)b, 8 * i - FIX_SHIFT) * 2.0L;
+            nh.etab[256 * i + b] = (double)std::exp(mode == PP_NOISE_INVERSE ? e : -e);
+        }
+    nh.d_etab = alloc_copy<double>(h, nh.etab);
     nh.d_gx = alloc_copy<uint64_t>(h, nh.gx);
     nh.d_gz = alloc_copy<uint64_t>(h, nh.gz);
     nh.d_glam = alloc_copy<int64_t>(h, nh.glam);
-    if (!nh.d_t1 || !nh.d_pair_off || !nh.d_pair_other || !nh.d_pair_id || !nh.d_t2 || !nh.d_gx ||
-        !nh.d_gz || !nh.d_glam)
+    if (!nh.d_t1 || !nh.d_shift || !nh.d_smask || !nh.d_pidx || !nh.d_c2 || !nh.d_gx || !nh.d_gz ||
+        !nh.d_glam || !nh.d_etab)
         return fail(h, PP_ERR_NOMEM, "noise table allocation failed");
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, PP_ERR_CUDA, "noise upload failed");
     h->noise[layer] = std::move(nh);
@@ -714,7 +829,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
 
     struct Scope {
         FILE* trace = nullptr;
-        cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        cudaEvent_t ev[2] = {nullptr, nullptr};
         ~Scope() {
             if (trace) fclose(trace);
             for (auto e : ev)
@@ -723,9 +838,13 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     } scope;
     if (const char* tp = getenv("PP_TRACE")) scope.trace = fopen(tp, "a");
     FILE* trace = scope.trace;
+    unsigned long long* phase = nullptr;
+    if (trace) {
+        phase = h->counters + CTR_PHASE;
+    }
     for (auto& e : scope.ev) CK(cudaEventCreate(&e));
 
-    const size_t tcap = (size_t)tier_cap(h, TIER_MAIN);
+    const size_t tcap = (size_t)tier_cap(h, 0);
     std::map<int, double> growth;   // observed output/input per sub-layer kind
     auto growth_of = [&](int s) {
         auto it = growth.find(h->sub_kind[s]);
@@ -752,10 +871,12 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     p.rpb = h->spill_b;
     p.rps = h->spill_s;
     p.rpcap = h->spill_cap;
+    p.spill_ctr = h->spill_ctr;
     p.spx = h->spill_grp.x;
     p.spz = h->spill_grp.z;
     p.spc = h->spill_grp.c;
     p.spcap = h->spill_cap;
+    p.phase = phase;
 
     // scatter the input into the first sub-layer's buckets
     int side = 0;
@@ -764,6 +885,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     unsigned long long ctr[CTR_COUNT];
     CK(cudaMemsetAsync(h->fill[side], 0, sizeof(uint32_t) * B, h->st));
     CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+    CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
     p.dx = h->arena[side].x;
     p.dz = h->arena[side].z;
     p.dc = h->arena[side].c;
@@ -776,7 +898,10 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input overflowed the overflow area");
-    CK(group_spill(h, side, B, C, ctr[CTR_SPILL], &launches));
+    unsigned long long n_spill = 0;
+    CK(spill_total(h, &n_spill));
+    CK(group_spill(h, side, B, C, n_spill, &launches));
+    unsigned long long n_over_in = n_spill;   // grouped overflow strings of the current layout
 
     size_t N = n_terms;
     size_t peak = N;
@@ -791,6 +916,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         const uint64_t nC = fin ? h->cap : h->cap / nB;
         if (!fin) CK(cudaMemsetAsync(h->fill[side ^ 1], 0, sizeof(uint32_t) * nB, h->st));
         CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+        CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
         CK(cudaMemsetAsync(h->delta, 0, sizeof(long long) * MAX_SITES, h->st));
         p.sx = h->arena[side].x;
         p.sz = h->arena[side].z;
@@ -809,38 +935,42 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         p.dC = nC;
         p.desc = h->d_subs + s;
         p.next = fin ? nullptr : h->d_subs + s + 1;
-        p.has_noise = d.noise >= 0;
+        // A noise map on the input observable itself stays in the processor's
+        // prologue (after the merge and truncation of the input); any other is
+        // applied by a streaming pass over the layout first.
+        p.has_noise = d.noise >= 0 && d.first;
         if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
-        float ms[3] = {0.f, 0.f, 0.f};
-        unsigned long long passed[2] = {0, 0};
-        // three tiers: main shared-memory tile, large shared-memory tile, global tile
-        for (int tier = TIER_MAIN; tier <= TIER_GLOBAL; ++tier) {
+        if (d.noise >= 0 && !d.first)
+            CK(apply_noise(h, h->noise[d.noise], side, B, C, n_over_in, p.eps, p.eps_f, &launches));
+        float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
+        unsigned long long passed[N_TIERS] = {0, 0, 0, 0};   // buckets tier t handed to t+1
+        for (int tier = 0; tier < N_TIERS; ++tier) {
             uint32_t n_items;
-            if (tier == TIER_MAIN) {
+            if (tier == 0) {
                 p.in_list = nullptr;
                 n_items = B;
             } else {
                 n_items = (uint32_t)passed[tier - 1];
                 if (n_items == 0) break;
-                p.in_list = tier == TIER_LARGE ? h->list_a : h->list_b;
+                p.in_list = h->pass_list[tier - 1];
             }
             p.n_list = n_items;
-            p.out_list = tier == TIER_MAIN ? h->list_a : (tier == TIER_LARGE ? h->list_b : nullptr);
+            p.out_list = tier < kGlobalTier ? h->pass_list[tier] : nullptr;
             p.work_ctr = CTR_WORK + tier;
-            p.defer_ctr = tier == TIER_MAIN ? CTR_DEFER1 : CTR_DEFER2;
+            p.defer_ctr = CTR_DEFER + (tier < kGlobalTier ? tier : 0);
             p.max_load = (uint32_t)(tier_cap(h, tier) * 3 / 4);
-            CK(cudaEventRecord(scope.ev[2 * tier], h->st));
+            CK(cudaEventRecord(scope.ev[0], h->st));
             CK(dispatch_process(h, p, tier, n_items, &launches));
-            CK(cudaEventRecord(scope.ev[2 * tier + 1], h->st));
+            CK(cudaEventRecord(scope.ev[1], h->st));
             CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
             CK(cudaStreamSynchronize(h->st));
-            cudaEventElapsedTime(&ms[tier], scope.ev[2 * tier], scope.ev[2 * tier + 1]);
+            cudaEventElapsedTime(&ms[tier], scope.ev[0], scope.ev[1]);
             stats.tier_launches[tier]++;
             stats.tier_ms[tier] += ms[tier];
             stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];
-            if (tier < TIER_GLOBAL) passed[tier] = ctr[tier == TIER_MAIN ? CTR_DEFER1 : CTR_DEFER2];
+            if (tier < kGlobalTier) passed[tier] = ctr[CTR_DEFER + tier];
         }
-        stats.fallback_buckets += (int)passed[1];
+        stats.fallback_buckets += (int)passed[kGlobalTier - 1];
         if (ctr[CTR_ERR_FALLBACK])
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s,
                         kFallbackCap);
@@ -848,7 +978,11 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
                         "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap,
                         h->spill_cap);
-        if (!fin) CK(group_spill(h, side ^ 1, nB, nC, ctr[CTR_SPILL], &launches));
+        unsigned long long n_spill_out = 0;
+        if (!fin) {
+            CK(spill_total(h, &n_spill_out));
+            CK(group_spill(h, side ^ 1, nB, nC, n_spill_out, &launches));
+        }
         long long dl[MAX_SITES];
         CK(cudaMemcpyAsync(dl, h->delta, sizeof(dl), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
@@ -862,13 +996,18 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         if (trace)
             fprintf(trace,
                     "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"n_in\": %zu, \"n_out\": %zu, "
-                    "\"buckets_in\": %u, \"buckets_out\": %u, \"to_large\": %llu, \"to_global\": %llu, "
-                    "\"spill\": %llu, \"ms_main\": %.4f, \"ms_large\": %.4f, \"ms_global\": %.4f}\n",
-                    s, d.cls, d.n_gates, N, Nout, B, nB, passed[0], passed[1],
-                    (unsigned long long)ctr[CTR_SPILL], ms[0], ms[1], ms[2]);
+                    "\"buckets_in\": %u, \"buckets_out\": %u, \"passed\": [%llu, %llu, %llu], "
+                    "\"spill\": %llu, \"ms\": [%.4f, %.4f, %.4f, %.4f], "
+                    "\"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
+                    "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu]}\n",
+                    s, d.cls, d.n_gates, N, Nout, B, nB, passed[0], passed[1], passed[2],
+                    n_spill_out, ms[0], ms[1], ms[2], ms[3], ctr[CTR_FAIL], ctr[CTR_FAIL + 1],
+                    ctr[CTR_FAIL + 2], ctr[CTR_PHASE], ctr[CTR_PHASE + 1], ctr[CTR_PHASE + 2], ctr[CTR_PHASE + 3],
+                    ctr[CTR_PHASE_CTA], ctr[CTR_PHASE_CTA + 1], ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3]);
         if (N > 0) growth[kind] = std::max(0.05, (double)Nout / (double)N);
         N = Nout;
         peak = std::max(peak, N);
+        n_over_in = n_spill_out;
         side ^= 1;
         B = nB;
         C = nC;

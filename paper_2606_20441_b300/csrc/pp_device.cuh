@@ -56,8 +56,23 @@ struct SubLayerDesc {
     double cs[MAX_SITES];         // cos(theta) by slot
     double sn[MAX_SITES];         // sin(theta) by slot
     int16_t order[MAX_SITES];     // listed index of the gate in each slot
+    int16_t slot_of[MAX_SITES];   // slot of each listed gate
     uint64_t gx[MAX_GEN][MAXW];   // generic generators
     uint64_t gz[MAX_GEN][MAXW];
+};
+
+// The fields of a sub-layer that a string's activity, gate mask and orbit key
+// need: small enough to stage in shared memory once per CTA.
+struct ActDesc {
+    int cls;
+    int ax, az, bx, bz;
+    int shift;
+    int n_gates;
+    int pad_;
+    uint64_t all[MAXW];
+    int16_t order[MAX_SITES];
+    const uint64_t* gx;           // generic generators [MAX_GEN][MAXW], in global memory
+    const uint64_t* gz;
 };
 
 // Sparse Pauli-Lindblad map evaluated from tables.  Letter code l = x + 2z
@@ -66,16 +81,21 @@ struct SubLayerDesc {
 struct NoiseDesc {
     int mode;                     // 0: exp(+2s), 1: exp(-2s)
     int n_generic;
-    const int64_t* t1;            // [n][4]   sum of lambda over 1-local generators on q
-                                  //          anticommuting with letter l
-    const int32_t* pair_off;      // [n+1]    CSR of pairs incident to each site
-    const int32_t* pair_other;    // [2P]     other site of the pair
-    const int32_t* pair_id;       // [2P]
-    const int64_t* t2;            // [P][16]  sum over 2-local generators on (a,b), index la + 4 lb
-                                  //          (a < b), anticommuting with the letter pair
+    int n_shift;                  // classes of 2-local generator supports (a, a + shift)
+    int n_sites;
+    const int64_t* t1;            // [n][4]  sum of lambda over every 1- or 2-local generator
+                                  //         touching q that anticommutes with letter l on q
+                                  //         (identity on the rest of its support)
+    const int32_t* shift;         // [n_shift] site distance of the class
+    const uint64_t* smask;        // [n_shift][W] first sites of the class's pairs
+    const int32_t* pidx;          // [n_shift][n] pair starting at site a in the class, or -1
+    const int64_t* c2;            // [P][16] correction for pairs with both sites in the
+                                  //         support: T2[la,lb] - T2[la,I] - T2[I,lb], index la + 4 lb
     const uint64_t* gen_x;        // [n_generic][W] heavier generators
     const uint64_t* gen_z;
     const int64_t* gen_lam;
+    const double* etab;           // [8][256] exp(+-2 * b * 2^(8i - 56)): factor tables by
+                                  //          byte i of the fixed-point exponent
 };
 
 // ----------------------------------------------------------------------------- bit helpers
@@ -168,11 +188,27 @@ __device__ __forceinline__ uint64_t hash_key(const uint64_t* x, const uint64_t* 
 
 // ----------------------------------------------------------------------------- activity
 
+// Row j of a generic-generator table, whether held as [MAX_GEN][MAXW] arrays
+// (SubLayerDesc) or as a flat pointer (ActDesc).
+__device__ __forceinline__ const uint64_t* gen_row(const uint64_t (*g)[MAXW], int j) { return g[j]; }
+__device__ __forceinline__ const uint64_t* gen_row(const uint64_t* g, int j) { return g + (size_t)j * MAXW; }
+
+__device__ __forceinline__ void make_act(const SubLayerDesc& s, ActDesc& d) {
+    d.cls = s.cls;
+    d.ax = s.ax; d.az = s.az; d.bx = s.bx; d.bz = s.bz;
+    d.shift = s.shift;
+    d.n_gates = s.n_gates;
+    for (int w = 0; w < MAXW; ++w) d.all[w] = s.all[w];
+    for (int i = 0; i < MAX_SITES; ++i) d.order[i] = s.order[i];
+    d.gx = &s.gx[0][0];
+    d.gz = &s.gz[0][0];
+}
+
 // Activity of string (x,z) in a sub-layer: bit per slot whose gate anticommutes
 // with the string.  Also the union of the acting generators' supports (per
 // letter bit), which masks the string into its orbit key.
-template <int W>
-__device__ __forceinline__ void activity(const SubLayerDesc& d, const uint64_t* x,
+template <int W, class D>
+__device__ __forceinline__ void activity(const D& d, const uint64_t* x,
                                          const uint64_t* z, uint64_t* A, uint64_t* Mx,
                                          uint64_t* Mz) {
     if (d.cls == CLS_LOCAL1 || d.cls == CLS_LOCAL2) {
@@ -205,12 +241,14 @@ __device__ __forceinline__ void activity(const SubLayerDesc& d, const uint64_t* 
 #pragma unroll
         for (int w = 0; w < W; ++w) Mx[w] = Mz[w] = 0ull;
         for (int j = 0; j < d.n_gates; ++j) {
-            if (anticommutes<W>(x, z, d.gx[j], d.gz[j])) {
+            const uint64_t* gxj = gen_row(d.gx, j);
+            const uint64_t* gzj = gen_row(d.gz, j);
+            if (anticommutes<W>(x, z, gxj, gzj)) {
                 a |= 1ull << j;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    Mx[w] |= d.gx[j][w] | d.gz[j][w];
-                    Mz[w] |= d.gx[j][w] | d.gz[j][w];
+                    Mx[w] |= gxj[w] | gzj[w];
+                    Mz[w] |= gxj[w] | gzj[w];
                 }
             }
         }
@@ -282,10 +320,23 @@ __device__ __forceinline__ void slot_generator(const SubLayerDesc& d, int slot, 
     }
 }
 
-// Orbit key of a string for sub-layer d and its bucket under 2^log2b buckets.
+// Multiply-xorshift hash of an orbit key for bucket selection.
 template <int W>
-__device__ __forceinline__ uint32_t bucket_of(const SubLayerDesc& d, const uint64_t* x,
-                                              const uint64_t* z, uint32_t bmask) {
+__device__ __forceinline__ uint64_t bucket_hash(const uint64_t* kx, const uint64_t* kz) {
+    uint64_t h = kx[0] * 0x9E3779B97F4A7C15ULL ^ (kz[0] + 0x632BE59BD9B4E019ULL) * 0xC2B2AE3D27D4EB4FULL;
+#pragma unroll
+    for (int w = 1; w < W; ++w)
+        h ^= kx[w] * 0xD6E8FEB86659FD93ULL ^ (kz[w] + 0x85EBCA77C2B2AE63ULL) * 0xFF51AFD7ED558CCDULL;
+    h ^= h >> 32;
+    h *= 0xD6E8FEB86659FD93ULL;
+    h ^= h >> 29;
+    return h;
+}
+
+// Orbit key of a string for sub-layer d and its bucket among bmask + 1 buckets.
+template <int W, class D>
+__device__ __forceinline__ uint32_t bucket_of(const D& d, const uint64_t* x, const uint64_t* z,
+                                              uint32_t bmask) {
     uint64_t A[W], Mx[W], Mz[W], kx[W], kz[W];
     activity<W>(d, x, z, A, Mx, Mz);
 #pragma unroll
@@ -293,31 +344,44 @@ __device__ __forceinline__ uint32_t bucket_of(const SubLayerDesc& d, const uint6
         kx[w] = x[w] & ~Mx[w];
         kz[w] = z[w] & ~Mz[w];
     }
-    return (uint32_t)(hash_key<W>(kx, kz) >> 20) & bmask;
+    return (uint32_t)(bucket_hash<W>(kx, kz) >> 20) & bmask;
 }
 
 // ----------------------------------------------------------------------------- noise
 
+// Exponent sum_{k: {P,E_k} = 0} lambda_k in 2^-56 fixed point: per-site terms
+// over supp(P) (which already hold the one-sided part of every pair), plus a
+// correction for each generator pair whose two sites are both in supp(P).
 template <int W>
 __device__ __forceinline__ int64_t noise_exponent(const NoiseDesc& nz, const uint64_t* x,
                                                   const uint64_t* z) {
     int64_t s = 0;
+    uint64_t sup[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        uint64_t sup = x[w] | z[w];
-        while (sup) {
-            int b = __ffsll((long long)sup) - 1;
-            sup &= sup - 1;
-            int q = 64 * w + b;
-            int lq = (int)((x[w] >> b) & 1ull) + 2 * (int)((z[w] >> b) & 1ull);
-            s += nz.t1[4 * q + lq];
-            for (int e = nz.pair_off[q]; e < nz.pair_off[q + 1]; ++e) {
-                int o = nz.pair_other[e];
-                int lo = (int)((x[o >> 6] >> (o & 63)) & 1ull) + 2 * (int)((z[o >> 6] >> (o & 63)) & 1ull);
-                if (lo != 0 && o < q) continue;      // pair already counted at its smaller site
-                int pid = nz.pair_id[e];
-                int idx = (q < o) ? (lq + 4 * lo) : (lo + 4 * lq);
-                s += nz.t2[16 * pid + idx];
+        sup[w] = x[w] | z[w];
+        uint64_t m = sup[w];
+        while (m) {
+            const int b = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const int lq = (int)((x[w] >> b) & 1ull) + 2 * (int)((z[w] >> b) & 1ull);
+            s += nz.t1[4 * (64 * w + b) + lq];
+        }
+    }
+    for (int c = 0; c < nz.n_shift; ++c) {
+        const int d = nz.shift[c];
+        uint64_t sh[W];
+        shr_words<W>(sup, d, sh);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t both = sup[w] & sh[w] & nz.smask[(size_t)c * W + w];
+            while (both) {
+                const int bpos = __ffsll((long long)both) - 1;
+                both &= both - 1;
+                const int a = 64 * w + bpos, bq = a + d;
+                const int la = (int)((x[w] >> bpos) & 1ull) + 2 * (int)((z[w] >> bpos) & 1ull);
+                const int lb = (int)((x[bq >> 6] >> (bq & 63)) & 1ull) + 2 * (int)((z[bq >> 6] >> (bq & 63)) & 1ull);
+                s += nz.c2[16 * nz.pidx[(size_t)c * nz.n_sites + a] + la + 4 * lb];
             }
         }
     }
@@ -327,9 +391,26 @@ __device__ __forceinline__ int64_t noise_exponent(const NoiseDesc& nz, const uin
     return s;
 }
 
-__device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t s) {
-    double sd = (double)s * 0x1p-56;
-    return nz.mode == 0 ? exp(__dmul_rn(2.0, sd)) : exp(__dmul_rn(-2.0, sd));
+// exp(+-2 s) for s = S * 2^-56 (S >= 0), as the product over the bytes of S of
+// host-tabulated factors: exp(a + b) = exp(a) exp(b), so at most seven FP64
+// multiplies instead of an FP64 exponential.  Each table entry is the exponential
+// correctly rounded to double; the product carries at most a few ulp.
+__device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t S, double) {
+    uint64_t u = (uint64_t)S;
+    double f = 1.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t byte = (uint32_t)(u >> (8 * i)) & 0xffu;
+        if (byte) f = __dmul_rn(f, nz.etab[256 * i + byte]);
+    }
+    return f;
+}
+
+// FP32 form: the exponential in single precision (the coefficient is stored in
+// single precision anyway); the exponent itself stays exact.
+__device__ __forceinline__ float noise_factor(const NoiseDesc& nz, int64_t S, float) {
+    const float s2 = __ll2float_rn((long long)S) * 0x1p-55f;   // 2 s
+    return nz.mode == 0 ? expf(s2) : expf(-s2);
 }
 
 // ----------------------------------------------------------------------------- coefficient ops

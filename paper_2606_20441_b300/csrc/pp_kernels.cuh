@@ -40,6 +40,7 @@ struct StepParams {
     uint32_t* rpb;
     uint32_t* rps;
     uint64_t rpcap;
+    unsigned long long* spill_ctr;   // [NSPILL] fill of each shard of the overflow area
 
     const SubLayerDesc* desc;
     const SubLayerDesc* next;     // nullptr when desc is final
@@ -57,47 +58,86 @@ struct StepParams {
     int work_ctr;                 // counter index of this launch's work queue
     int defer_ctr;                // counter index of out_list's length
     uint32_t max_load;            // buckets with more strings are passed on
+    unsigned long long* phase;    // [4] cycles spent in load, prologue, rounds, output (tier 0),
+                                  // accumulated when tracing; nullptr otherwise
 };
 
 enum {
-    CTR_WORK = 0,        // work queues, one per tier
-    CTR_WORK2 = 1,
-    CTR_WORK3 = 2,
-    CTR_OUT = 3,         // terms written (next layout or final)
-    CTR_PROLOGUE = 4,    // live terms after the prologue (merge / noise)
-    CTR_DEFER1 = 5,      // buckets passed from the main tier to the large tier
-    CTR_DEFER2 = 6,      // buckets passed from the large tier to the global tier
-    CTR_ERR_REGION = 7,  // strings dropped: overflow area or result full
-    CTR_ERR_FALLBACK = 8,// buckets too large even for the global tier
-    CTR_SPILL = 9,       // strings written to the destination overflow area
-    CTR_LOADED = 12,     // strings loaded by completed buckets, per tier (12..14)
-    CTR_EMITTED = 15,    // strings written by completed buckets, per tier (15..17)
-    CTR_COUNT = 20
+    CTR_WORK = 0,        // work queues, one per tier (0..3)
+    CTR_OUT = 4,         // terms written (next layout or final)
+    CTR_PROLOGUE = 5,    // live terms after the prologue (merge / noise)
+    CTR_DEFER = 6,       // buckets passed from tier t to tier t+1 (6..8)
+    CTR_ERR_REGION = 9,  // strings dropped: overflow area or result full
+    CTR_ERR_FALLBACK = 10, // buckets too large even for the global tier
+    CTR_SPILL = 11,      // strings written to the destination overflow area
+    CTR_LOADED = 12,     // strings loaded by completed buckets, per tier (12..15)
+    CTR_EMITTED = 16,    // strings written by completed buckets, per tier (16..19)
+    CTR_FAIL = 20,       // buckets passed on, by reason (20..23): load, entry pool, hash, list
+    CTR_SPILL_TOTAL = 24,// scratch of the overflow grouping
+    CTR_PHASE = 28,      // tier-0 cycles per phase when tracing (28..31)
+    CTR_PHASE_CTA = 32,  // CTA-tier cycles per phase when tracing (32..35)
+    CTR_COUNT = 36
 };
 
-// Working set of one bucket.  Arrays live in shared memory (main kernel) or in a
-// per-CTA global scratch slice (fallback kernel); both paths run the same code.
-template <int W, typename T>
+constexpr int N_TIERS = 4;
+constexpr int NSPILL = 64;   // shards of the overflow area (one atomic counter each)
+
+enum { FAIL_LOAD = 1, FAIL_POOL = 2, FAIL_HASH = 3, FAIL_CHUNK = 4 };
+
+__device__ __forceinline__ int16_t atomic_cas_idx(int16_t* a, int16_t cmp, int16_t val) {
+    return (int16_t)atomicCAS(reinterpret_cast<unsigned short*>(a), (unsigned short)cmp, (unsigned short)val);
+}
+__device__ __forceinline__ int32_t atomic_cas_idx(int32_t* a, int32_t cmp, int32_t val) {
+    return atomicCAS(a, cmp, val);
+}
+
+// Working set of one bucket.  Arrays live in shared memory (the shared-memory
+// tiers) or in a per-CTA slice of global scratch memory (the global tier); all
+// tiers run the same code.  I is the entry-index type (int16_t in shared
+// memory, int32_t in global memory).
+template <int W, typename T, typename I>
 struct Tile {
-    uint64_t* x;      // [W][cap]
+    uint64_t* x;      // [W][cap] string
     uint64_t* z;      // [W][cap]
-    T* c;             // current coefficient, 0 = not live
+    uint64_t* g;      // [W][cap] gates of the sub-layer still to apply (listed-order bits)
+    T* c;             // coefficient, 0 = not live
     T* cn;            // coefficient after the current round
-    int32_t* pj;      // partner index this round; -1 none; -2 inactive
-    int16_t* ps;      // slot of this round's gate
-    int8_t* ph;       // +1/-1: sign of the sin-branch contribution to the partner
-    int8_t* rv;       // revived by a partner this round
-    int32_t* hash;    // [hcap] entry index or -1
+    uint8_t* gi;      // listed index of this round's gate
+    I* hash;          // [hcap] entry index or -1 (insert-only)
+    I* act;           // [2][cap] strings with gates left: this round's list, the next one's
     int cap;
     int hcap;
-    int* n;           // number of entries
-    int* flag;        // capacity exceeded
-    int* kmax;
+    int hbits;
+    int* n;           // entries used
+    int* flag;        // nonzero (a FAIL_* reason): the bucket goes to the next tier
     int* live;
+    int* nact;        // [2] lengths of the two active lists
 };
 
+constexpr int NWARPS = 16;    // warps per CTA of every tier (512 threads)
+
+// Gates of the current sub-layer in listed order, staged in shared memory.
 template <int W, typename T>
-__device__ __forceinline__ void tile_key(const Tile<W, T>& t, int i, uint64_t* x, uint64_t* z) {
+struct GateTab {
+    uint64_t rx[64 * W][W];
+    uint64_t rz[64 * W][W];
+    T cs[64 * W];
+    T sn[64 * W];
+};
+
+template <int W>
+__device__ __forceinline__ uint32_t tile_hash(const uint64_t* x, const uint64_t* z, int hbits) {
+    uint64_t h = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        h += x[w] * (0x9E3779B97F4A7C15ULL + 2 * w) + z[w] * (0xC2B2AE3D27D4EB4FULL + 2 * w);
+    h ^= h >> 31;
+    h *= 0xD6E8FEB86659FD93ULL;
+    return (uint32_t)(h >> (64 - hbits));
+}
+
+template <int W, typename T, typename I>
+__device__ __forceinline__ void tile_key(const Tile<W, T, I>& t, int i, uint64_t* x, uint64_t* z) {
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         x[w] = t.x[(size_t)w * t.cap + i];
@@ -105,8 +145,8 @@ __device__ __forceinline__ void tile_key(const Tile<W, T>& t, int i, uint64_t* x
     }
 }
 
-template <int W, typename T>
-__device__ __forceinline__ bool tile_key_eq(const Tile<W, T>& t, int i, const uint64_t* x,
+template <int W, typename T, typename I>
+__device__ __forceinline__ bool tile_key_eq(const Tile<W, T, I>& t, int i, const uint64_t* x,
                                             const uint64_t* z) {
     bool eq = true;
 #pragma unroll
@@ -115,54 +155,57 @@ __device__ __forceinline__ bool tile_key_eq(const Tile<W, T>& t, int i, const ui
     return eq;
 }
 
-template <int W, typename T>
-__device__ __forceinline__ int tile_lookup(const Tile<W, T>& t, const uint64_t* x, const uint64_t* z) {
-    uint32_t h = (uint32_t)hash_key<W>(x, z) & (uint32_t)(t.hcap - 1);
+// Entries are never removed from the table (a truncated string keeps its slot
+// and may be revived), so a lookup of a key inserted earlier never meets an
+// empty slot before it, whatever other warps insert meanwhile.
+template <int W, typename T, typename I>
+__device__ __forceinline__ int tile_lookup(const Tile<W, T, I>& t, const uint64_t* x, const uint64_t* z) {
+    uint32_t h = tile_hash<W>(x, z, t.hbits);
     for (int probe = 0; probe < t.hcap; ++probe) {
-        int s = t.hash[h];
+        int s = (int)t.hash[h];
         if (s < 0) return -1;
-        if (tile_key_eq<W, T>(t, s, x, z)) return s;
+        if (tile_key_eq<W, T, I>(t, s, x, z)) return s;
         h = (h + 1) & (uint32_t)(t.hcap - 1);
     }
     return -1;
 }
 
-// Inserts entry idx (key already stored).  merge: if the key is present, add c
-// into the existing entry instead and leave idx dead.
-template <int W, typename T>
-__device__ __forceinline__ void tile_insert(const Tile<W, T>& t, int idx, const uint64_t* x,
+// Inserts entry idx (key and coefficient already stored).  merge: if the key is
+// present, add the coefficient into the existing entry and leave idx dead.
+template <int W, typename T, typename I>
+__device__ __forceinline__ void tile_insert(const Tile<W, T, I>& t, int idx, const uint64_t* x,
                                             const uint64_t* z, bool merge) {
-    uint32_t h = (uint32_t)hash_key<W>(x, z) & (uint32_t)(t.hcap - 1);
+    uint32_t h = tile_hash<W>(x, z, t.hbits);
     for (int probe = 0; probe < t.hcap; ++probe) {
-        int prev = atomicCAS(&t.hash[h], -1, idx);
+        int prev = (int)atomic_cas_idx(&t.hash[h], (I)-1, (I)idx);
         if (prev < 0) return;
-        if (merge && tile_key_eq<W, T>(t, prev, x, z)) {
+        if (merge && tile_key_eq<W, T, I>(t, prev, x, z)) {
             atomicAdd(&t.c[prev], t.c[idx]);
             t.c[idx] = T(0);
             return;
         }
         h = (h + 1) & (uint32_t)(t.hcap - 1);
     }
-    atomicExch(t.flag, 1);
+    atomicExch(t.flag, (int)FAIL_HASH);
 }
 
-template <int W, typename T>
-__device__ __forceinline__ T load_coef(const void* base, size_t i);
-template <>
-__device__ __forceinline__ double load_coef<1, double>(const void* base, size_t i) {
-    return static_cast<const double*>(base)[i];
+// Appends entry i to active list `which` (warp-aggregated; all lanes of the
+// warp must call it together, `want` false for lanes that append nothing).
+template <int W, typename T, typename I>
+__device__ __forceinline__ void act_append(const Tile<W, T, I>& t, int which, bool want, int i) {
+    const unsigned msk = __ballot_sync(0xffffffffu, want);
+    if (!msk) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(msk) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&t.nact[which], __popc(msk));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) t.act[(size_t)which * t.cap + base + __popc(msk & ((1u << lane) - 1u))] = (I)i;
 }
-template <>
-__device__ __forceinline__ double load_coef<2, double>(const void* base, size_t i) {
-    return static_cast<const double*>(base)[i];
-}
-template <>
-__device__ __forceinline__ float load_coef<1, float>(const void* base, size_t i) {
-    return static_cast<const float*>(base)[i];
-}
-template <>
-__device__ __forceinline__ float load_coef<2, float>(const void* base, size_t i) {
-    return static_cast<const float*>(base)[i];
+
+template <typename T>
+__device__ __forceinline__ T load_coef(const void* base, size_t i) {
+    return static_cast<const T*>(base)[i];
 }
 
 template <typename T>
@@ -188,8 +231,11 @@ __device__ __forceinline__ void emit(const StepParams& p, uint32_t nb, const uin
         static_cast<T*>(p.dc)[pos] = c;
         return;
     }
-    unsigned long long k = atomicAdd(&p.counters[CTR_SPILL], 1ull);
-    if (k < p.rpcap) {
+    const uint64_t shard_cap = p.rpcap / NSPILL;
+    const int shard = (int)((blockIdx.x * 8 + (threadIdx.x >> 5)) % NSPILL);
+    unsigned long long k = atomicAdd(&p.spill_ctr[shard], 1ull);
+    if (k < shard_cap) {
+        k += (unsigned long long)shard * shard_cap;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             p.rpx[(size_t)w * p.rpcap + k] = x[w];
@@ -207,21 +253,34 @@ __device__ __forceinline__ void emit(const StepParams& p, uint32_t nb, const uin
 // noise map), gate rounds, then writes the surviving strings into the next
 // layout's buckets (or the compact final array).  Returns false, having
 // written nothing, when the bucket does not fit the tile.
-template <int W, typename T>
-__device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_t b,
-                               int* s_delta) {
+//
+// The whole CTA works on one bucket; rounds are separated by CTA barriers.
+// This serves the buckets too large for one warp (see k_process_warp).
+template <int W, typename T, typename I>
+__device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab, const ActDesc& ad,
+                               const ActDesc& adn, const StepParams& p, uint32_t b, int* s_delta) {
     const SubLayerDesc& d = *p.desc;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31;
     const T eps = eps_of<T>(p);
     const uint32_t n_in = p.sfill[b];
+    long long clk0 = p.phase ? clock64() : 0;
+    auto phase_mark = [&](int ph) {
+        if (p.phase && tid == 0) {
+            long long clk1 = clock64();
+            atomicAdd(&p.phase[4 + ph], (unsigned long long)(clk1 - clk0));
+            clk0 = clk1;
+        }
+    };
 
-    for (int i = tid; i < t.hcap; i += nt) t.hash[i] = -1;
+    for (int i = tid; i < t.hcap; i += nt) t.hash[i] = (I)-1;
     for (int i = tid; i < MAX_SITES; i += nt) s_delta[i] = 0;
     if (tid == 0) {
         *t.n = (int)n_in;
-        *t.flag = (n_in > p.max_load) ? 1 : 0;
-        *t.kmax = 0;
+        *t.flag = (n_in > p.max_load) ? (int)FAIL_LOAD : 0;
         *t.live = 0;
+        t.nact[0] = 0;
+        t.nact[1] = 0;
     }
     __syncthreads();
     if (*t.flag) return false;
@@ -243,140 +302,208 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
             t.x[(size_t)w * t.cap + i] = x[w];
             t.z[(size_t)w * t.cap + i] = z[w];
         }
-        t.c[i] = load_coef<W, T>(reg ? p.sc : p.spc, src);
-        t.rv[i] = 0;
+        t.c[i] = load_coef<T>(reg ? p.sc : p.spc, src);
         if (d.first) __threadfence_block();
-        tile_insert<W, T>(t, i, x, z, d.first != 0);
+        tile_insert<W, T, I>(t, i, x, z, d.first != 0);
     }
     __syncthreads();
+    phase_mark(0);
 
-    // ---- prologue: truncation of the merged input; noise map
-    int my_live = 0, my_k = 0;
-    for (int i = tid; i < (int)n_in; i += nt) {
-        T c = t.c[i];
-        uint64_t x[W], z[W];
-        tile_key<W, T>(t, i, x, z);
-        if (d.first && c != T(0)) {
-            if (Coef<T>::small(c, eps) || (p.w_max >= 0 && weight_of<W>(x, z) > p.w_max)) c = T(0);
-        }
-        if (p.has_noise && c != T(0)) {
-            double f = noise_factor(p.noise, noise_exponent<W>(p.noise, x, z));
-            c = Coef<T>::mul(c, T(f));
-            if (Coef<T>::small(c, eps)) c = T(0);
-        }
-        t.c[i] = c;
-        if (c != T(0)) {
-            ++my_live;
-            uint64_t A[W], Mx[W], Mz[W];
-            activity<W>(d, x, z, A, Mx, Mz);
-            int k = count_active<W>(A);
-            my_k = k > my_k ? k : my_k;
-        }
-    }
-    if (my_live) atomicAdd(t.live, my_live);
-    if (my_k) atomicMax(t.kmax, my_k);
-    __syncthreads();
-    const int kmax = *t.kmax;
-    const int live0 = *t.live;
-
-    // ---- gate rounds: round r applies each string's r-th acting gate
-    for (int r = 0; r < kmax; ++r) {
-        const int nr = *t.n;
-        for (int i = tid; i < nr; i += nt) {
-            int state = -2;
+    // ---- prologue: truncation of the merged input, noise map, and each live
+    // string's gate mask (gates of the sub-layer that act on it, listed order)
+    int my_live = 0;
+    for (int i0 = 0; i0 < (int)n_in; i0 += nt) {
+        const int i = i0 + tid;
+        bool has_gates = false;
+        if (i < (int)n_in) {
             T c = t.c[i];
-            if (c != T(0)) {
-                uint64_t x[W], z[W], A[W], Mx[W], Mz[W];
-                tile_key<W, T>(t, i, x, z);
-                activity<W>(d, x, z, A, Mx, Mz);
-                if (count_active<W>(A) > r) {
-                    int slot = select_slot<W>(d, A, r);
-                    uint64_t rx[W], rz[W], qx[W], qz[W];
-                    slot_generator<W>(d, slot, rx, rz);
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        qx[w] = x[w] ^ rx[w];
-                        qz[w] = z[w] ^ rz[w];
-                    }
-                    state = tile_lookup<W, T>(t, qx, qz);
-                    // i R P = i^{1+e} (R xor P): sign of P's sin-branch into its partner
-                    int e = product_phase<W>(rx, rz, x, z);
-                    t.ph[i] = ((1 + e) & 3) == 0 ? 1 : -1;
-                    t.ps[i] = (int16_t)slot;
-                }
+            uint64_t x[W], z[W];
+            tile_key<W, T, I>(t, i, x, z);
+            if (d.first && c != T(0)) {
+                if (Coef<T>::small(c, eps) || (p.w_max >= 0 && weight_of<W>(x, z) > p.w_max)) c = T(0);
             }
-            t.pj[i] = state;
-        }
-        __syncthreads();
-        for (int i = tid; i < nr; i += nt) {
-            int j = t.pj[i];
-            if (j == -2) continue;
-            int slot = t.ps[i];
-            T cs = T(d.cs[slot]), sn = T(d.sn[slot]);
-            T c = t.c[i];
-            int phi = t.ph[i];
-            T c2 = (j >= 0) ? t.c[j] : T(0);
-            if (j >= 0 && c2 != T(0)) {
-                // partner P xor R is live: both members rotate; the partner's
-                // contribution into P carries the opposite sign (i R Q = -phi P)
-                t.cn[i] = Coef<T>::rot(cs, c, sn, c2, -phi);
-            } else {
-                t.cn[i] = Coef<T>::mul(cs, c);
-                T v = Coef<T>::mul(sn, c);
-                if (phi < 0) v = -v;
-                if (!Coef<T>::small(v, eps)) {
-                    uint64_t x[W], z[W], rx[W], rz[W];
-                    tile_key<W, T>(t, i, x, z);
-                    slot_generator<W>(d, slot, rx, rz);
+            if (p.has_noise && c != T(0)) {
+                const T f = noise_factor(p.noise, noise_exponent<W>(p.noise, x, z), T(0));
+                c = Coef<T>::mul(c, f);
+                if (Coef<T>::small(c, eps)) c = T(0);
+            }
+            t.c[i] = c;
+            uint64_t gm[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) gm[w] = 0ull;
+            if (c != T(0)) {
+                ++my_live;
+                uint64_t A[W], Mx[W], Mz[W];
+                activity<W>(ad, x, z, A, Mx, Mz);
+                if (ad.cls == CLS_GENERIC) {
+                    gm[0] = A[0];
+                } else {
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
-                        x[w] ^= rx[w];
-                        z[w] ^= rz[w];
-                    }
-                    if (p.w_max < 0 || weight_of<W>(x, z) <= p.w_max) {
-                        atomicAdd(&s_delta[d.order[slot]], 1);
-                        if (j >= 0) {
-                            t.cn[j] = v;          // revive a string truncated earlier
-                            t.rv[j] = 1;
-                        } else {
-                            int idx = atomicAdd(t.n, 1);
-                            if (idx >= t.cap) {
-                                atomicExch(t.flag, 1);
-                            } else {
-#pragma unroll
-                                for (int w = 0; w < W; ++w) {
-                                    t.x[(size_t)w * t.cap + idx] = x[w];
-                                    t.z[(size_t)w * t.cap + idx] = z[w];
-                                }
-                                t.c[idx] = v;
-                                t.pj[idx] = -2;
-                                t.rv[idx] = 0;
-                                tile_insert<W, T>(t, idx, x, z, false);
-                            }
+                        uint64_t a = A[w];
+                        while (a) {
+                            int bpos = __ffsll((long long)a) - 1;
+                            a &= a - 1;
+                            int gidx = ad.order[64 * w + bpos];
+                            gm[gidx >> 6] |= 1ull << (gidx & 63);
                         }
                     }
                 }
+#pragma unroll
+                for (int w = 0; w < W; ++w) has_gates |= gm[w] != 0ull;
             }
+#pragma unroll
+            for (int w = 0; w < W; ++w) t.g[(size_t)w * t.cap + i] = gm[w];
+        }
+        act_append<W, T, I>(t, 0, has_gates, i);
+    }
+    if (my_live) atomicAdd(t.live, my_live);
+    __syncthreads();
+    const int live0 = *t.live;
+    phase_mark(1);
+
+    // ---- gate rounds.  Round r: every listed string applies the next gate of
+    // its mask (orbit members share the mask, so a string and its partner use
+    // the same gate), then the next round's list keeps the strings still live
+    // with gates left.  A string's partner under its round gate is unique to
+    // it, so the lookup and the rotation share one pass; new and revived
+    // strings join the next round's list.  Counters are bumped once per warp
+    // (votes), never once per thread: in a large orbit every string applies the
+    // same gate in the same round.
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r <= 64 * W; ++r) {
+        const int cur = r & 1, nxt = cur ^ 1;
+        const int na = t.nact[cur];
+        if (na == 0) break;
+        const I* L = t.act + (size_t)cur * t.cap;
+        for (int k0 = 0; k0 < na; k0 += nt) {
+            const int k = k0 + tid;
+            bool create = false, revive = false;
+            int j = -1, gg = -1;
+            T v = T(0);
+            uint64_t qx[W], qz[W], gm[W];
+            if (k < na) {
+                const int i = (int)L[k];
+                uint64_t x[W], z[W];
+                tile_key<W, T, I>(t, i, x, z);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    gm[w] = t.g[(size_t)w * t.cap + i];
+                    if (gg < 0 && gm[w]) {
+                        gg = 64 * w + __ffsll((long long)gm[w]) - 1;
+                        gm[w] &= gm[w] - 1;
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    t.g[(size_t)w * t.cap + i] = gm[w];
+                    qx[w] = x[w] ^ tab.rx[gg][w];
+                    qz[w] = z[w] ^ tab.rz[gg][w];
+                }
+                t.gi[i] = (uint8_t)gg;
+                j = tile_lookup<W, T, I>(t, qx, qz);
+                // i R P = i^{1+e} (R xor P): sign of P's sin-branch into its partner
+                const int e = product_phase<W>(tab.rx[gg], tab.rz[gg], x, z);
+                const int phi = ((1 + e) & 3) == 0 ? 1 : -1;
+                const T cs = tab.cs[gg], sn = tab.sn[gg];
+                const T c = t.c[i];
+                const T c2 = (j >= 0) ? t.c[j] : T(0);
+                if (j >= 0 && c2 != T(0)) {
+                    // both members of the pair rotate; the partner's contribution
+                    // into P carries the opposite sign (i R Q = -phi P)
+                    t.cn[i] = Coef<T>::rot(cs, c, sn, c2, -phi);
+                } else {
+                    t.cn[i] = Coef<T>::mul(cs, c);
+                    v = Coef<T>::mul(sn, c);
+                    if (phi < 0) v = -v;
+                    if (!Coef<T>::small(v, eps) && (p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max)) {
+                        if (j >= 0) revive = true;
+                        else create = true;
+                    }
+                }
+            }
+            // entry indices for new strings: one atomic per warp
+            const unsigned cm = __ballot_sync(FULL, create);
+            int nbase = 0;
+            if (cm) {
+                if (lane == __ffs(cm) - 1) nbase = atomicAdd(t.n, __popc(cm));
+                nbase = __shfl_sync(FULL, nbase, __ffs(cm) - 1);
+            }
+            int idx = j;
+            if (create) {
+                idx = nbase + __popc(cm & lt);
+                if (idx >= t.cap) {
+                    atomicExch(t.flag, (int)FAIL_POOL);
+                    create = false;
+                }
+            }
+            if (create) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    t.x[(size_t)w * t.cap + idx] = qx[w];
+                    t.z[(size_t)w * t.cap + idx] = qz[w];
+                }
+            }
+            const bool born = create || revive;
+            bool join = false;
+            if (born) {
+                // a new string, or one truncated earlier revived: it joins the
+                // orbit with the gates the orbit has left
+                t.c[idx] = v;
+                bool more = false;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    t.g[(size_t)w * t.cap + idx] = gm[w];
+                    more |= gm[w] != 0ull;
+                }
+                if (create) {
+                    __threadfence_block();
+                    tile_insert<W, T, I>(t, idx, qx, qz, false);
+                }
+                join = more;
+            }
+            // per-gate count of strings born this round: lanes of equal gate add once
+            {
+                const unsigned bm = __ballot_sync(FULL, born);
+                if (bm) {
+                    const unsigned same = __match_any_sync(FULL, born ? gg : -1);
+                    if (born && lane == __ffs(same) - 1) atomicAdd(&s_delta[gg], __popc(same));
+                }
+            }
+            act_append<W, T, I>(t, nxt, join, idx);
         }
         __syncthreads();
         if (*t.flag) return false;
-        const int nn = *t.n;
-        for (int i = tid; i < nr; i += nt) {
-            if (t.pj[i] != -2) {
+        for (int k0 = 0; k0 < na; k0 += nt) {
+            const int k = k0 + tid;
+            bool keep = false, dropped = false;
+            int i = 0, gd = -1;
+            if (k < na) {
+                i = (int)L[k];
                 T v = t.cn[i];
                 if (Coef<T>::small(v, eps)) {
                     v = T(0);
-                    atomicAdd(&s_delta[d.order[t.ps[i]]], -1);
+                    dropped = true;
+                    gd = t.gi[i];
                 }
                 t.c[i] = v;
-            } else if (t.rv[i]) {
-                t.c[i] = t.cn[i];
-                t.rv[i] = 0;
+                if (v != T(0)) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) keep |= t.g[(size_t)w * t.cap + i] != 0ull;
+                }
             }
+            const unsigned dm = __ballot_sync(FULL, dropped);
+            if (dm) {
+                const unsigned same = __match_any_sync(FULL, gd);
+                if (dropped && lane == __ffs(same) - 1) atomicAdd(&s_delta[gd], -__popc(same));
+            }
+            act_append<W, T, I>(t, nxt, keep, i);
         }
-        (void)nn;
+        if (tid == 0) t.nact[cur] = 0;
         __syncthreads();
     }
+    phase_mark(2);
 
     // ---- output
     if (d.final_) {
@@ -411,7 +538,6 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
             ++pos;
         }
     } else {
-        const SubLayerDesc& dn = *p.next;
         const uint32_t bmask = p.dB - 1;
         const int nf = *t.n;
         int cnt = 0;
@@ -420,8 +546,8 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
             if (c == T(0)) continue;
             ++cnt;
             uint64_t x[W], z[W];
-            tile_key<W, T>(t, i, x, z);
-            uint32_t nb = bucket_of<W>(dn, x, z, bmask);
+            tile_key<W, T, I>(t, i, x, z);
+            uint32_t nb = bucket_of<W>(adn, x, z, bmask);
             emit<W, T>(p, nb, x, z, c);
         }
         if (cnt) {
@@ -430,6 +556,7 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
         }
     }
     __syncthreads();
+    phase_mark(3);
     if (tid == 0) {
         atomicAdd(&p.counters[CTR_PROLOGUE], (unsigned long long)live0);
         atomicAdd(&p.counters[CTR_LOADED + (p.work_ctr - CTR_WORK)], (unsigned long long)n_in);
@@ -441,44 +568,73 @@ __device__ bool process_bucket(const Tile<W, T>& t, const StepParams& p, uint32_
     return true;
 }
 
-template <int W, typename T>
-__host__ __device__ constexpr size_t tile_bytes_per_entry() {
-    return 2 * W * sizeof(uint64_t) + 2 * sizeof(T) + sizeof(int32_t) + sizeof(int16_t) + 2 +
-           2 * sizeof(int32_t);
+// Hash slots of a tile: the power of two at least twice its entries.
+__host__ __device__ constexpr size_t tile_hcap(size_t cap) {
+    size_t h = 1;
+    while (h < 2 * cap) h <<= 1;
+    return h;
 }
 
-template <int W, typename T>
-__device__ __forceinline__ Tile<W, T> carve_tile(unsigned char* mem, int cap, int* ctl) {
-    Tile<W, T> t;
+// Bytes carve_tile lays out for a tile of `cap` entries.
+template <int W, typename T, typename I>
+__host__ __device__ constexpr size_t tile_layout_bytes(size_t cap) {
+    return sizeof(uint64_t) * W * cap * 3 + sizeof(T) * cap * 2 + sizeof(I) * tile_hcap(cap) +
+           sizeof(I) * 2 * cap + cap;
+}
+
+template <int W, typename T, typename I>
+__device__ __forceinline__ Tile<W, T, I> carve_tile(unsigned char* mem, int cap, int* ctl) {
+    Tile<W, T, I> t;
     t.cap = cap;
-    t.hcap = 2 * cap;
+    t.hcap = (int)tile_hcap((size_t)cap);
+    t.hbits = 31 - __clz(t.hcap);
     unsigned char* q = mem;
     t.x = reinterpret_cast<uint64_t*>(q); q += sizeof(uint64_t) * W * cap;
     t.z = reinterpret_cast<uint64_t*>(q); q += sizeof(uint64_t) * W * cap;
+    t.g = reinterpret_cast<uint64_t*>(q); q += sizeof(uint64_t) * W * cap;
     t.c = reinterpret_cast<T*>(q); q += sizeof(T) * cap;
     t.cn = reinterpret_cast<T*>(q); q += sizeof(T) * cap;
-    t.hash = reinterpret_cast<int32_t*>(q); q += sizeof(int32_t) * 2 * cap;
-    t.pj = reinterpret_cast<int32_t*>(q); q += sizeof(int32_t) * cap;
-    t.ps = reinterpret_cast<int16_t*>(q); q += sizeof(int16_t) * cap;
-    t.ph = reinterpret_cast<int8_t*>(q); q += cap;
-    t.rv = reinterpret_cast<int8_t*>(q); q += cap;
+    t.hash = reinterpret_cast<I*>(q); q += sizeof(I) * t.hcap;
+    t.act = reinterpret_cast<I*>(q); q += sizeof(I) * 2 * cap;
+    t.gi = reinterpret_cast<uint8_t*>(q); q += cap;
     t.n = ctl + 0;
     t.flag = ctl + 1;
-    t.kmax = ctl + 2;
-    t.live = ctl + 3;
+    t.live = ctl + 2;
+    t.nact = ctl + 4;
     return t;
+}
+
+template <int W, typename T>
+__device__ __forceinline__ void load_gate_table(GateTab<W, T>& tab, const SubLayerDesc& d) {
+    for (int g = threadIdx.x; g < d.n_gates && g < 64 * W; g += blockDim.x) {
+        int slot = d.cls == CLS_GENERIC ? g : d.slot_of[g];
+        uint64_t rx[W], rz[W];
+        slot_generator<W>(d, slot, rx, rz);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            tab.rx[g][w] = rx[w];
+            tab.rz[g][w] = rz[w];
+        }
+        tab.cs[g] = T(d.cs[slot]);
+        tab.sn[g] = T(d.sn[slot]);
+    }
 }
 
 // Shared-memory tiers: persistent CTAs take buckets from a work queue (all
 // buckets, or the list a smaller tier passed on); a bucket that does not fit is
 // passed to the next tier.
-template <int W, typename T>
-__global__ void k_process(StepParams p, int cap) {
+template <int W, typename T, int NT>
+__global__ void __launch_bounds__(NT) k_process(StepParams p, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int ctl[4];
+    __shared__ int ctl[8];
     __shared__ int s_delta[MAX_SITES];
     __shared__ uint32_t s_b;
-    Tile<W, T> t = carve_tile<W, T>(smem, cap, ctl);
+    __shared__ GateTab<W, T> tab;
+    __shared__ ActDesc s_ad, s_adn;
+    Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem, cap, ctl);
+    if (threadIdx.x == 0) make_act(*p.desc, s_ad);
+    if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
+    load_gate_table<W, T>(tab, *p.desc);
     const uint32_t n_items = p.in_list ? p.n_list : p.sB;
     for (;;) {
         if (threadIdx.x == 0) s_b = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);
@@ -487,8 +643,9 @@ __global__ void k_process(StepParams p, int cap) {
         if (k >= n_items) break;
         const uint32_t b = p.in_list ? p.in_list[k] : k;
         if (p.sfill[b] != 0) {
-            bool ok = process_bucket<W, T>(t, p, b, s_delta);
+            bool ok = process_bucket<W, T, int16_t>(t, tab, s_ad, s_adn, p, b, s_delta);
             if (!ok && threadIdx.x == 0) {
+                atomicAdd(&p.counters[CTR_FAIL + (*t.flag - 1)], 1ull);
                 if (p.out_list) {
                     unsigned long long j = atomicAdd(&p.counters[p.defer_ctr], 1ull);
                     p.out_list[j] = b;
@@ -504,18 +661,27 @@ __global__ void k_process(StepParams p, int cap) {
 // Global tier for the largest buckets: the same processor with the tile in a
 // per-CTA slice of global scratch memory.
 template <int W, typename T>
-__global__ void k_process_global(StepParams p, unsigned char* scratch, size_t slice_bytes, int cap) {
-    __shared__ int ctl[4];
+__global__ void __launch_bounds__(NWARPS * 32) k_process_global(StepParams p, unsigned char* scratch,
+                                                                size_t slice_bytes, int cap) {
+    __shared__ int ctl[8];
     __shared__ int s_delta[MAX_SITES];
     __shared__ uint32_t s_k;
-    Tile<W, T> t = carve_tile<W, T>(scratch + slice_bytes * blockIdx.x, cap, ctl);
+    __shared__ GateTab<W, T> tab;
+    __shared__ ActDesc s_ad, s_adn;
+    Tile<W, T, int32_t> t = carve_tile<W, T, int32_t>(scratch + slice_bytes * blockIdx.x, cap, ctl);
+    if (threadIdx.x == 0) make_act(*p.desc, s_ad);
+    if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
+    load_gate_table<W, T>(tab, *p.desc);
     for (;;) {
         if (threadIdx.x == 0) s_k = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);
         __syncthreads();
         const uint32_t k = s_k;
         if (k >= p.n_list) break;
-        bool ok = process_bucket<W, T>(t, p, p.in_list[k], s_delta);
-        if (!ok && threadIdx.x == 0) atomicAdd(&p.counters[CTR_ERR_FALLBACK], 1ull);
+        bool ok = process_bucket<W, T, int32_t>(t, tab, s_ad, s_adn, p, p.in_list[k], s_delta);
+        if (!ok && threadIdx.x == 0) {
+            atomicAdd(&p.counters[CTR_FAIL + (*t.flag - 1)], 1ull);
+            atomicAdd(&p.counters[CTR_ERR_FALLBACK], 1ull);
+        }
         __syncthreads();
     }
 }
@@ -564,10 +730,12 @@ __global__ void k_spill_offsets(const uint32_t* fill, uint32_t nB, uint64_t C, u
 
 template <int W, typename T>
 __global__ void k_spill_move(const uint64_t* rx, const uint64_t* rz, const T* rc, const uint32_t* rb,
-                             const uint32_t* rs, uint64_t rcap, uint64_t n, const uint64_t* soff,
-                             uint64_t* ox, uint64_t* oz, T* oc, uint64_t ocap) {
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+                             const uint32_t* rs, uint64_t rcap, const unsigned long long* shard_fill,
+                             const uint64_t* soff, uint64_t* ox, uint64_t* oz, T* oc, uint64_t ocap) {
+    const uint64_t shard_cap = rcap / NSPILL;
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < shard_cap * NSPILL;
          k += (uint64_t)gridDim.x * blockDim.x) {
+        if (k % shard_cap >= shard_fill[k / shard_cap]) continue;
         uint64_t dst = soff[rb[k]] + rs[k];
         if (dst >= ocap) continue;
 #pragma unroll
@@ -577,6 +745,87 @@ __global__ void k_spill_move(const uint64_t* rx, const uint64_t* rz, const T* rc
         }
         oc[dst] = rc[k];
     }
+}
+
+// ----------------------------------------------------------------------------- noise map
+
+// Shared-memory copy of a noise map's tables (sizes fixed per map).
+struct NoiseSmem {
+    size_t t1, shift, smask, pidx, c2, etab;   // byte offsets
+    size_t bytes;
+};
+
+__host__ __device__ inline NoiseSmem noise_smem_layout(int n_sites, int n_shift, int n_pairs, int W) {
+    NoiseSmem L;
+    size_t o = 0;
+    L.etab = o; o += sizeof(double) * 8 * 256;
+    L.t1 = o; o += sizeof(int64_t) * 4 * (size_t)n_sites;
+    L.c2 = o; o += sizeof(int64_t) * 16 * (size_t)n_pairs;
+    L.smask = o; o += sizeof(uint64_t) * (size_t)n_shift * W;
+    L.shift = o; o += sizeof(int32_t) * (size_t)n_shift;
+    L.pidx = o; o += sizeof(int32_t) * (size_t)n_shift * n_sites;
+    L.bytes = (o + 15) & ~(size_t)15;
+    return L;
+}
+
+// Applies an inverse (or forward) Pauli-Lindblad map in place to every string
+// of a bucketed layout: the buckets' regions, then the grouped overflow area.
+// The map's tables are staged in shared memory; strings are streamed once.
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_noise(const uint64_t* x, const uint64_t* z, T* c, uint64_t cap,
+                                               const uint32_t* fill, uint32_t B, uint64_t C,
+                                               const uint64_t* ox, const uint64_t* oz, T* oc, uint64_t ocap,
+                                               uint64_t n_over, NoiseDesc nz, int n_pairs, double eps,
+                                               float eps_f) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const NoiseSmem L = noise_smem_layout(nz.n_sites, nz.n_shift, n_pairs, W);
+    {
+        auto cp = [&](size_t off, const void* src, size_t bytes) {
+            const uint32_t* s32 = static_cast<const uint32_t*>(src);
+            uint32_t* d32 = reinterpret_cast<uint32_t*>(smem + off);
+            for (size_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d32[i] = s32[i];
+        };
+        if (sizeof(T) == 8) cp(L.etab, nz.etab, sizeof(double) * 8 * 256);
+        cp(L.t1, nz.t1, sizeof(int64_t) * 4 * (size_t)nz.n_sites);
+        cp(L.c2, nz.c2, sizeof(int64_t) * 16 * (size_t)n_pairs);
+        cp(L.smask, nz.smask, sizeof(uint64_t) * (size_t)nz.n_shift * W);
+        cp(L.shift, nz.shift, sizeof(int32_t) * (size_t)nz.n_shift);
+        cp(L.pidx, nz.pidx, sizeof(int32_t) * (size_t)nz.n_shift * nz.n_sites);
+    }
+    __syncthreads();
+    NoiseDesc sn = nz;
+    sn.etab = reinterpret_cast<const double*>(smem + L.etab);
+    sn.t1 = reinterpret_cast<const int64_t*>(smem + L.t1);
+    sn.c2 = reinterpret_cast<const int64_t*>(smem + L.c2);
+    sn.smask = reinterpret_cast<const uint64_t*>(smem + L.smask);
+    sn.shift = reinterpret_cast<const int32_t*>(smem + L.shift);
+    sn.pidx = reinterpret_cast<const int32_t*>(smem + L.pidx);
+    const T e = sizeof(T) == 8 ? T(eps) : T(eps_f);
+
+    auto apply = [&](const uint64_t* ax, const uint64_t* az, T* ac, uint64_t acap, uint64_t i) {
+        T v = ac[i];
+        if (v == T(0)) return;
+        uint64_t xx[W], zz[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            xx[w] = ax[(size_t)w * acap + i];
+            zz[w] = az[(size_t)w * acap + i];
+        }
+        v = Coef<T>::mul(v, noise_factor(sn, noise_exponent<W>(sn, xx, zz), T(0)));
+        if (Coef<T>::small(v, e)) v = T(0);
+        ac[i] = v;
+    };
+    // regions: one warp per bucket
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t b = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < B; b += warps) {
+        const uint64_t f = fill[b] < C ? fill[b] : C;
+        for (uint64_t i = lane; i < f; i += 32) apply(x, z, c, cap, b * C + i);
+    }
+    // grouped overflow strings
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_over;
+         k += (uint64_t)gridDim.x * blockDim.x)
+        apply(ox, oz, oc, ocap, k);
 }
 
 // ----------------------------------------------------------------------------- expectation

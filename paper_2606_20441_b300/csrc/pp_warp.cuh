@@ -1,0 +1,384 @@
+// Tier 0 of the sub-layer processor: one warp per bucket.
+//
+// Most buckets hold a few dozen to a few hundred strings.  Giving each such
+// bucket to one warp, with its own slice of shared memory, removes every
+// CTA-wide barrier from the gate rounds: a round needs only __syncwarp, list
+// appends and new-entry indices come from warp votes (no shared-memory
+// atomics on counters), and the ~20 warps resident on an SM work on
+// independent buckets, hiding each other's latencies.  The arithmetic and the
+// per-gate semantics are those of process_bucket (pp_kernels.cuh); buckets that
+// do not fit a warp tile are passed to the CTA tiers.
+#pragma once
+
+#include "pp_kernels.cuh"
+
+namespace pp {
+
+constexpr int WARP_TILE_WARPS = 4;   // warps per CTA; each owns its buckets
+
+template <int W, typename T>
+__host__ __device__ constexpr size_t warp_tile_bytes(size_t cap) {
+    return (tile_layout_bytes<W, T, int16_t>(cap) + 15) & ~(size_t)15;
+}
+
+// Per-warp accumulators folded into the CTA's at the end of a bucket.
+struct WarpAcc {
+    unsigned long long prologue, loaded, emitted;
+};
+
+template <int W, typename T>
+__device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& tab, const ActDesc& ad,
+                            const ActDesc& adn, const StepParams& p, uint32_t b, int* wdelta, WarpAcc& acc) {
+    const SubLayerDesc& d = *p.desc;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const T eps = eps_of<T>(p);
+    const int n_in = (int)p.sfill[b];
+    if (n_in > (int)p.max_load) {
+        if (lane == 0) *t.flag = (int)FAIL_LOAD;
+        return false;
+    }
+    long long clk0 = p.phase ? clock64() : 0, clk1 = 0;
+    auto phase_mark = [&](int ph) {
+        if (p.phase) {
+            clk1 = clock64();
+            if (lane == 0) atomicAdd(&p.phase[ph], (unsigned long long)(clk1 - clk0));
+            clk0 = clk1;
+        }
+    };
+    for (int i = lane; i < t.hcap; i += 32) t.hash[i] = (int16_t)-1;
+    for (int i = lane; i < 64 * W; i += 32) wdelta[i] = 0;
+    if (lane == 0) *t.flag = 0;
+    __syncwarp();
+
+    // ---- load: the bucket's region, then its overflow strings
+    const size_t base = (size_t)b * p.sC;
+    const size_t obase = ((uint64_t)n_in > p.sC) ? (size_t)p.soff[b] : 0;
+    for (int i = lane; i < n_in; i += 32) {
+        uint64_t x[W], z[W];
+        const bool reg = (uint64_t)i < p.sC;
+        const size_t src = reg ? base + i : obase + (i - p.sC);
+        const uint64_t* ax = reg ? p.sx : p.spx;
+        const uint64_t* az = reg ? p.sz : p.spz;
+        const size_t acap = reg ? p.scap : p.spcap;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            x[w] = ax[(size_t)w * acap + src];
+            z[w] = az[(size_t)w * acap + src];
+            t.x[(size_t)w * t.cap + i] = x[w];
+            t.z[(size_t)w * t.cap + i] = z[w];
+        }
+        t.c[i] = load_coef<T>(reg ? p.sc : p.spc, src);
+        if (d.first) __threadfence_block();
+        tile_insert<W, T, int16_t>(t, i, x, z, d.first != 0);
+    }
+    __syncwarp();
+    phase_mark(0);
+
+    // ---- prologue: truncation of the merged input, noise map, gate masks
+    int na = 0, live = 0;
+    for (int i0 = 0; i0 < n_in; i0 += 32) {
+        const int i = i0 + lane;
+        bool alive = false, has_gates = false;
+        if (i < n_in) {
+            T c = t.c[i];
+            uint64_t x[W], z[W];
+            tile_key<W, T, int16_t>(t, i, x, z);
+            if (d.first && c != T(0)) {
+                if (Coef<T>::small(c, eps) || (p.w_max >= 0 && weight_of<W>(x, z) > p.w_max)) c = T(0);
+            }
+            if (p.has_noise && c != T(0)) {
+                const T f = noise_factor(p.noise, noise_exponent<W>(p.noise, x, z), T(0));
+                c = Coef<T>::mul(c, f);
+                if (Coef<T>::small(c, eps)) c = T(0);
+            }
+            t.c[i] = c;
+            uint64_t gm[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) gm[w] = 0ull;
+            if (c != T(0)) {
+                alive = true;
+                uint64_t A[W], Mx[W], Mz[W];
+                activity<W>(ad, x, z, A, Mx, Mz);
+                if (ad.cls == CLS_GENERIC) {
+                    gm[0] = A[0];
+                } else {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        uint64_t a = A[w];
+                        while (a) {
+                            int bpos = __ffsll((long long)a) - 1;
+                            a &= a - 1;
+                            int gidx = ad.order[64 * w + bpos];
+                            gm[gidx >> 6] |= 1ull << (gidx & 63);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) has_gates |= gm[w] != 0ull;
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) t.g[(size_t)w * t.cap + i] = gm[w];
+        }
+        live += __popc(__ballot_sync(FULL, alive));
+        const unsigned am = __ballot_sync(FULL, has_gates);
+        if (has_gates) t.act[na + __popc(am & lt)] = (int16_t)i;
+        na += __popc(am);
+    }
+    __syncwarp();
+    if (*(volatile int*)t.flag) return false;
+    phase_mark(1);
+
+    // ---- gate rounds (see process_bucket): lookup and rotation in one pass,
+    // then the commit; new-entry indices and list slots come from warp votes
+    int n = n_in;
+    for (int r = 0; r <= 64 * W && na > 0; ++r) {
+        const int16_t* L = t.act + (size_t)(r & 1) * t.cap;
+        int16_t* Ln = t.act + (size_t)((r & 1) ^ 1) * t.cap;
+        int nn = 0;
+        bool over = false;
+        for (int k0 = 0; k0 < na; k0 += 32) {
+            const int k = k0 + lane;
+            bool create = false, revive = false;
+            int i = 0, j = -1, gg = 0;
+            T v = T(0);
+            uint64_t qx[W], qz[W], gm[W];
+            if (k < na) {
+                i = (int)L[k];
+                uint64_t x[W], z[W];
+                tile_key<W, T, int16_t>(t, i, x, z);
+                gg = -1;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    gm[w] = t.g[(size_t)w * t.cap + i];
+                    if (gg < 0 && gm[w]) {
+                        gg = 64 * w + __ffsll((long long)gm[w]) - 1;
+                        gm[w] &= gm[w] - 1;
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    t.g[(size_t)w * t.cap + i] = gm[w];
+                    qx[w] = x[w] ^ tab.rx[gg][w];
+                    qz[w] = z[w] ^ tab.rz[gg][w];
+                }
+                t.gi[i] = (uint8_t)gg;
+                j = tile_lookup<W, T, int16_t>(t, qx, qz);
+                // i R P = i^{1+e} (R xor P): sign of P's sin-branch into its partner
+                const int e = product_phase<W>(tab.rx[gg], tab.rz[gg], x, z);
+                const int phi = ((1 + e) & 3) == 0 ? 1 : -1;
+                const T cs = tab.cs[gg], sn = tab.sn[gg];
+                const T c = t.c[i];
+                const T c2 = (j >= 0) ? t.c[j] : T(0);
+                if (j >= 0 && c2 != T(0)) {
+                    // both members of the pair rotate; the partner's contribution
+                    // into P carries the opposite sign (i R Q = -phi P)
+                    t.cn[i] = Coef<T>::rot(cs, c, sn, c2, -phi);
+                } else {
+                    t.cn[i] = Coef<T>::mul(cs, c);
+                    v = Coef<T>::mul(sn, c);
+                    if (phi < 0) v = -v;
+                    if (!Coef<T>::small(v, eps) && (p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max)) {
+                        if (j >= 0) revive = true;
+                        else create = true;
+                    }
+                }
+            }
+            const unsigned cm = __ballot_sync(FULL, create);
+            int idx = j;
+            if (create) {
+                idx = n + __popc(cm & lt);
+                if (idx >= t.cap) {
+                    over = true;
+                    create = false;
+                }
+            }
+            n += __popc(cm);
+            if (create) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    t.x[(size_t)w * t.cap + idx] = qx[w];
+                    t.z[(size_t)w * t.cap + idx] = qz[w];
+                }
+            }
+            bool join = false;
+            {
+                const bool born = create || revive;
+                if (__ballot_sync(FULL, born)) {
+                    const unsigned same = __match_any_sync(FULL, born ? gg : -1);
+                    if (born && lane == __ffs(same) - 1) wdelta[gg] += __popc(same);
+                }
+                __syncwarp();
+            }
+            if (create || revive) {
+                // a new string, or one truncated earlier revived: it joins the
+                // orbit with the gates the orbit has left
+                t.c[idx] = v;
+                bool more = false;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    t.g[(size_t)w * t.cap + idx] = gm[w];
+                    more |= gm[w] != 0ull;
+                }
+                if (create) {
+                    __threadfence_block();
+                    tile_insert<W, T, int16_t>(t, idx, qx, qz, false);
+                }
+                join = more;
+            }
+            const unsigned jm = __ballot_sync(FULL, join);
+            if (join) Ln[nn + __popc(jm & lt)] = (int16_t)idx;
+            nn += __popc(jm);
+        }
+        __syncwarp();
+        const bool any_over = __any_sync(FULL, over);
+        if (any_over || *(volatile int*)t.flag) {
+            if (lane == 0) *t.flag = any_over ? (int)FAIL_POOL : (int)FAIL_HASH;
+            return false;
+        }
+        __syncwarp();
+        for (int k0 = 0; k0 < na; k0 += 32) {
+            const int k = k0 + lane;
+            bool keep = false, dropped = false;
+            int i = 0, gd = -1;
+            if (k < na) {
+                i = (int)L[k];
+                T v = t.cn[i];
+                if (Coef<T>::small(v, eps)) {
+                    v = T(0);
+                    dropped = true;
+                    gd = t.gi[i];
+                }
+                t.c[i] = v;
+                if (v != T(0)) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) keep |= t.g[(size_t)w * t.cap + i] != 0ull;
+                }
+            }
+            if (__ballot_sync(FULL, dropped)) {
+                const unsigned same = __match_any_sync(FULL, gd);
+                if (dropped && lane == __ffs(same) - 1) wdelta[gd] -= __popc(same);
+                __syncwarp();
+            }
+            const unsigned km = __ballot_sync(FULL, keep);
+            if (keep) Ln[nn + __popc(km & lt)] = (int16_t)i;
+            nn += __popc(km);
+        }
+        __syncwarp();
+        na = nn;
+    }
+
+    phase_mark(2);
+
+    // ---- output
+    unsigned long long emitted = 0;
+    if (d.final_) {
+        int cnt = 0;
+        for (int i = lane; i < n; i += 32) cnt += t.c[i] != T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+        unsigned long long pos = 0;
+        if (lane == 0 && cnt) pos = atomicAdd(&p.counters[CTR_OUT], (unsigned long long)cnt);
+        pos = __shfl_sync(FULL, pos, 0);
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const bool lv = i < n && t.c[i] != T(0);
+            const unsigned lm = __ballot_sync(FULL, lv);
+            if (lv) {
+                const unsigned long long q = pos + __popc(lm & lt);
+                if (q < p.dcap) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        p.dx[(size_t)w * p.dcap + q] = t.x[(size_t)w * t.cap + i];
+                        p.dz[(size_t)w * p.dcap + q] = t.z[(size_t)w * t.cap + i];
+                    }
+                    static_cast<T*>(p.dc)[q] = t.c[i];
+                } else {
+                    atomicAdd(&p.counters[CTR_ERR_REGION], 1ull);
+                }
+            }
+            pos += __popc(lm);
+        }
+        emitted = (unsigned long long)cnt;
+    } else {
+        const uint32_t bmask = p.dB - 1;
+        int cnt = 0;
+        for (int i = lane; i < n; i += 32) {
+            T c = t.c[i];
+            if (c == T(0)) continue;
+            ++cnt;
+            uint64_t x[W], z[W];
+            tile_key<W, T, int16_t>(t, i, x, z);
+            emit<W, T>(p, bucket_of<W>(adn, x, z, bmask), x, z, c);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+        emitted = (unsigned long long)cnt;
+    }
+    phase_mark(3);
+    acc.prologue += (unsigned long long)live;
+    acc.loaded += (unsigned long long)n_in;
+    acc.emitted += emitted;
+    return true;
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(32 * WARP_TILE_WARPS) k_process_warp(StepParams p, int cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ GateTab<W, T> tab;
+    __shared__ int s_delta[MAX_SITES];
+    __shared__ int s_wdelta[WARP_TILE_WARPS][64 * W];   // per-bucket counts by listed gate
+    __shared__ int s_ctl[WARP_TILE_WARPS][8];
+    __shared__ unsigned long long s_acc[3];
+    __shared__ ActDesc s_ad, s_adn;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < MAX_SITES; i += blockDim.x) s_delta[i] = 0;
+    if (threadIdx.x < 3) s_acc[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) make_act(*p.desc, s_ad);
+    if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
+    load_gate_table<W, T>(tab, *p.desc);
+    __syncthreads();
+
+    Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem + warp_tile_bytes<W, T>(cap) * wid, cap, s_ctl[wid]);
+    WarpAcc acc{0ull, 0ull, 0ull};
+    const uint32_t n_items = p.in_list ? p.n_list : p.sB;
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= n_items) break;
+        const uint32_t b = p.in_list ? p.in_list[k] : k;
+        if (p.sfill[b] == 0) continue;
+        if (warp_bucket<W, T>(t, tab, s_ad, s_adn, p, b, s_wdelta[wid], acc)) {
+            for (int i = lane; i < 64 * W; i += 32)
+                if (s_wdelta[wid][i]) atomicAdd(&s_delta[i], s_wdelta[wid][i]);
+        } else if (lane == 0) {
+            atomicAdd(&p.counters[CTR_FAIL + (*t.flag - 1)], 1ull);
+            unsigned long long j = atomicAdd(&p.counters[p.defer_ctr], 1ull);
+            p.out_list[j] = b;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        atomicAdd(&s_acc[0], acc.prologue);
+        atomicAdd(&s_acc[1], acc.loaded);
+        atomicAdd(&s_acc[2], acc.emitted);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < MAX_SITES; i += blockDim.x)
+        if (s_delta[i])
+            atomicAdd(reinterpret_cast<unsigned long long*>(&p.delta[i]),
+                      (unsigned long long)(long long)s_delta[i]);   // two's complement
+    if (threadIdx.x == 0) {
+        const int tier = p.work_ctr - CTR_WORK;
+        if (s_acc[0]) atomicAdd(&p.counters[CTR_PROLOGUE], s_acc[0]);
+        if (s_acc[1]) atomicAdd(&p.counters[CTR_LOADED + tier], s_acc[1]);
+        if (s_acc[2]) {
+            atomicAdd(&p.counters[CTR_EMITTED + tier], s_acc[2]);
+            if (!p.desc->final_) atomicAdd(&p.counters[CTR_OUT], s_acc[2]);
+        }
+    }
+}
+
+}  // namespace pp

@@ -356,11 +356,12 @@ def random_circuit(seed: int, n: int, n_layers: int, max_gates: int = 3, max_sup
                    noise_prob: float = 0.6, n_gen: int = 4, rate_hi: float = 0.05,
                    n_obs: int = 3, eps: float = 0.0, w_max: int = -1,
                    modes: Sequence[int] = (NOISE_INVERSE, NOISE_FORWARD),
-                   angles: Optional[Sequence[float]] = None) -> Instance:
+                   angles: Optional[Sequence[float]] = None, gen_weight: int = 2) -> Instance:
     """Random circuit of generic Pauli rotations (any axis, any weight up to
     max_support).  Gates inside a layer act on disjoint qubits, so they commute.
     Noise layers carry n_gen random generators of weight 1-2.  Angles are drawn
-    uniformly from [-pi, pi) unless a list of allowed angles is given."""
+    uniformly from [-pi, pi) unless a list of allowed angles is given; noise
+    generators have weight 1..gen_weight."""
     rng = SplitMix64(seed)
     W = n_words(n)
     gx, gz, th, lay, noise = [], [], [], [], []
@@ -382,7 +383,7 @@ def random_circuit(seed: int, n: int, n_layers: int, max_gates: int = 3, max_sup
         if rng.uniform() < noise_prob:
             ex, ez, lam = [], [], []
             for _ in range(n_gen):
-                k = 1 + rng.randint(min(2, n))
+                k = 1 + rng.randint(min(gen_weight, n))
                 sites = []
                 pool = list(range(n))
                 for _ in range(k):

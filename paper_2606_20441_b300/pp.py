@@ -48,9 +48,9 @@ class pp_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int),
                 ("fallback_buckets", ctypes.c_int),
                 ("seconds", ctypes.c_double),
-                ("tier_launches", ctypes.c_int * 3),
-                ("tier_ms", ctypes.c_double * 3),
-                ("tier_strings", ctypes.c_double * 3),
+                ("tier_launches", ctypes.c_int * 4),
+                ("tier_ms", ctypes.c_double * 4),
+                ("tier_strings", ctypes.c_double * 4),
                 ("bytes_per_string", ctypes.c_double)]
 
 

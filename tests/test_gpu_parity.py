@@ -60,6 +60,14 @@ def test_random_generic_circuits(pp, seed):
     check(pp, inst)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_heavy_noise_generators(pp, seed):
+    """Generators of weight up to 4 (the generic noise path) next to 1- and 2-local ones."""
+    inst = inputs.random_circuit(200 + seed, 12 + 30 * seed, n_layers=8, eps=1e-4, max_gates=4,
+                                 rate_hi=0.05, n_gen=12, gen_weight=4)
+    check(pp, inst)
+
+
 @pytest.mark.parametrize("steps,eps", [(2, 1e-5), (3, 1e-5), (3, 1e-4)])
 def test_tfim_6x6(pp, steps, eps):
     _, got, info = check(pp, inputs.workload_6x6(steps=steps, eps=eps))
