@@ -152,6 +152,32 @@ pp_status pp_get_stats(const pp_handle* h, pp_stats* out);
 /* Description of the last failure on this handle ("" if none).  Valid until the next call. */
 const char* pp_last_error(const pp_handle* h);
 
+/* Largest term count pp_expect_noalloc accepts (2^27). */
+#define PP_NOALLOC_MAX_TERMS ((size_t)134217728)
+
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory when they need <0..0|O~|0..0>: work recorded
+ * while a stream is captured into a CUDA graph, applications whose own memory
+ * pool owns the device and forbids other allocations, latency-critical paths
+ * that must not enter the CUDA allocator.  It computes the same exact
+ * fixed-point sum as pp_expect, over terms in the caller's device buffers,
+ * without a handle and without allocating: its scratch (one 128-bit partial
+ * per 16384 terms, 128 KiB) is a fixed array in the library's device image,
+ * present on every GPU that loads the library until the process exits.
+ *   x_dev      [n_terms][W] X masks in device memory (only X decides diagonality)
+ *   c_dev      [n_terms] FP64 coefficients in device memory
+ *   value_dev  device pointer receiving the double result
+ *   cuda_stream  stream to run on (NULL: legacy default stream); the call only
+ *              enqueues work -- read value_dev after synchronising the stream
+ * The first call on a device looks up the array's device address (set-up, with
+ * that device current); make that first call before any stream capture begins.
+ * Every call shares the one array, so calls that overlap on the GPU race and
+ * must be serialised by the caller.
+ * Errors: PP_ERR_ARG (n_qubits outside 1..128, null pointers), PP_ERR_CAPACITY
+ * (n_terms above PP_NOALLOC_MAX_TERMS), PP_ERR_CUDA. */
+pp_status pp_expect_noalloc(int n_qubits, size_t n_terms, const uint64_t* x_dev, const double* c_dev,
+                            double* value_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,8 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpp.so")
-SOURCES = ["pp.cu"]
-HEADERS = ["pp_device.cuh", "pp_kernels.cuh"]
+SOURCES = ["pp.cu", "pp_noalloc.cu"]
+HEADERS = ["pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "-diag-suppress", "177"]
 

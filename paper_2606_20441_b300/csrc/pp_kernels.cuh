@@ -830,20 +830,6 @@ __global__ void __launch_bounds__(256) k_noise(const uint64_t* x, const uint64_t
 
 // ----------------------------------------------------------------------------- expectation
 
-// trunc(v * 2^80) as a 128-bit two's-complement integer (|v| < 2^46).
-__device__ __forceinline__ __int128 to_fixed80(double v) {
-    uint64_t bits = (uint64_t)__double_as_longlong(v);
-    int ex = (int)((bits >> 52) & 0x7ff);
-    if (ex == 0) return 0;
-    uint64_t m = (bits & 0xfffffffffffffULL) | (1ULL << 52);
-    int sh = ex - 1075 + 80;
-    __int128 mag;
-    if (sh <= -64) mag = 0;
-    else if (sh < 0) mag = (__int128)(m >> (-sh));
-    else mag = ((__int128)m) << sh;
-    return (bits >> 63) ? -mag : mag;
-}
-
 // Sum of c over strings with x == 0, in exact fixed point; one partial per CTA.
 template <int W, typename T>
 __global__ void k_expect(const uint64_t* x, const T* c, uint64_t cap, uint64_t n,

@@ -61,7 +61,9 @@ class PPError(RuntimeError):
 
 
 EXPORTED = ["pp_default_options", "pp_create", "pp_destroy", "pp_load_circuit", "pp_load_noise",
-            "pp_propagate", "pp_expect", "pp_export_terms", "pp_get_stats", "pp_last_error"]
+            "pp_propagate", "pp_expect", "pp_export_terms", "pp_get_stats", "pp_last_error",
+            "pp_expect_noalloc"]
+NOALLOC_MAX_TERMS = 1 << 27
 
 _lib = None
 
@@ -87,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     L.pp_get_stats.argtypes = [vp, ctypes.POINTER(pp_stats)]
     L.pp_last_error.argtypes = [vp]
     L.pp_last_error.restype = ctypes.c_char_p
+    L.pp_expect_noalloc.argtypes = [ctypes.c_int, sz, vp, vp, vp, vp]
     for f in EXPORTED:
         if f not in ("pp_default_options", "pp_last_error"):
             getattr(L, f).restype = ctypes.c_int
@@ -205,6 +208,14 @@ class Handle:
         self.pp_propagate(inst.obs_x, inst.obs_z, inst.obs_c,
                           inst.eps if eps is None else eps,
                           inst.w_max if w_max is None else w_max)
+
+
+def pp_expect_noalloc(n_qubits: int, n_terms: int, x_dev: int, c_dev: int, value_dev: int,
+                      stream: Optional[int] = None) -> int:
+    """<0..0|O~|0..0> of terms in caller-owned device buffers (x masks row-major
+    [n_terms][W], FP64 coefficients), written to the device double at value_dev,
+    without any device allocation.  Returns the pp_status."""
+    return load_library().pp_expect_noalloc(int(n_qubits), int(n_terms), x_dev, c_dev, value_dev, stream)
 
 
 @dataclasses.dataclass
