@@ -41,9 +41,9 @@ from paper_2606_20441_b300 import inputs  # noqa: E402
 
 METRIC = "Pauli-term updates/s"
 UNIT = "updates/s"
-PROFILE = os.path.join(ROOT, "profiles", "k_process_tfim7x8.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_process_warp_tfim7x8.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2606_20441_b300", "csrc", f)
-                  for f in ("pp_device.cuh", "pp_kernels.cuh")]
+                  for f in ("pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh")]
 
 
 def workload(args):
@@ -289,7 +289,7 @@ def ours_arm(args, rank, world, local_rank):
     main_ms_avg = tier_ms[0] / max(1, tier_launches[0])
     main_bytes = tier_strings[0] * bps / max(1, tier_launches[0])
     achieved = main_bytes / (main_ms_avg / 1000.0) / 1e9 if main_ms_avg > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "k_process (tier 0: 128-thread CTAs, 512-string tiles)",
+    roofline = {"bound": "hbm", "kernel": "k_process_warp (tier 0: one warp per bucket, 248-string tiles)",
                 "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": main_bytes, "avg_launch_ms": main_ms_avg,
@@ -318,6 +318,71 @@ def ours_arm(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def pool_arm(args, rank, world, local_rank):
+    """Many independent instances on one GPU: the 64-instance batch (all
+    requests present at once) or a Poisson request stream, through the serving
+    loop's workers (each worker: own CUDA stream, own handles, a share of the
+    HBM budget).  Also times the same instances one after another on a single
+    FP64 handle -- the plain single-instance path -- for comparison."""
+    import torch
+    from paper_2606_20441_b300 import build, pp, serving
+    torch.cuda.set_device(local_rank)
+    build.build()
+    if args.workload == "batch64":
+        insts = inputs.workload_batch64(eps=1e-5, w_max=10)
+        reqs = [inputs.Request(i, 0.0, inst) for i, inst in enumerate(insts)]
+        cfg = {"workload": "batch64_eps1e-05_wmax10", "instances": len(insts),
+               "lattices": "4x4..8x8", "trotter_steps": "5-25", "coefficients": "fp%d" % args.precision,
+               "parallelism": "replicas", "workers": args.workers, "l2": "working set larger than L2"}
+    else:
+        reqs = inputs.workload_serving(count=args.requests, rate_hz=args.rate, eps_set=(1e-4, 1e-5), w_max=10)
+        insts = [r.instance for r in reqs]
+        cfg = {"workload": "serving_poisson%gHz_eps1e-4..1e-5_wmax10" % args.rate, "requests": len(reqs),
+               "lattices": "4x4..10x10", "trotter_steps": "5-30", "coefficients": "fp%d" % args.precision,
+               "parallelism": "replicas", "workers": args.workers, "l2": "working set larger than L2"}
+    budget = 0.6 * torch.cuda.mem_get_info()[0]
+    ex = serving.GpuExecutor(n_workers=args.workers, hbm_budget_bytes=budget, precision=args.precision)
+    # warm-up: every worker runs a small request
+    small = inputs.workload_batch64(count=args.workers, eps=1e-4, w_max=6)
+    serving.Server(ex, n_workers=args.workers).serve([inputs.Request(i, 0.0, x) for i, x in enumerate(small)])
+    torch.cuda.synchronize()
+    out = serving.Server(ex, n_workers=args.workers).serve(reqs)
+    torch.cuda.synchronize()
+    ex.close()
+    summ = serving.summarize(out)
+    # the plain single-instance FP64 path over the same instances, one at a time
+    single_upd, single_s = 0.0, 0.0
+    if not args.no_single:
+        h1 = pp.Handle(64, precision=64, max_terms=int(budget / 2.6 / 24))
+        h2 = None
+        for inst in insts:
+            h = h1
+            if inst.W == 2:
+                h2 = h2 or pp.Handle(128, precision=64, max_terms=int(budget / 2.6 / 40 / 2))
+                h = h2
+            h.load_instance(inst)
+            t = time.perf_counter()
+            try:
+                h.run_instance(inst)
+                h.pp_expect()
+                single_upd += h.pp_get_stats().updates
+            except pp.PPError:
+                pass
+            single_s += time.perf_counter() - t
+        h1.close()
+        if h2:
+            h2.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": summ["updates_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": summ["span_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f%d" % args.precision, "data": "synthetic",
+            "config": cfg, "served": summ["served"], "failed": summ["failed"],
+            "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
+            "single_instance_fp64_updates_per_s": single_upd / single_s if single_s > 0 else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +395,10 @@ def main():
     ap.add_argument("--sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--no-single", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank = int(os.environ.get("RANK", "0"))
@@ -337,6 +406,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+    elif args.workload in ("batch64", "serve"):
+        pool_arm(args, rank, world, local_rank)
     else:
         ours_arm(args, rank, world, local_rank)
 

@@ -129,6 +129,26 @@ pp_status pp_expect(pp_handle* h, double* value);
 pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, double* c,
                           size_t* n_out);
 
+/* One propagation of a batch: the arguments of pp_propagate. */
+typedef struct {
+    size_t n_terms;
+    const uint64_t* ox;
+    const uint64_t* oz;
+    const double* oc;
+    double eps;
+    int w_max;
+} pp_batch_item;
+
+/* Runs pp_propagate(handles[i], items[i]) for i < n, many at once: up to
+ * max_threads host threads take items in order and drive their handles'
+ * sub-layer loops, so the propagations overlap on the GPU.  Give every handle
+ * its own stream (pp_options.cuda_stream) -- handles on one stream serialise.
+ * Handles must be distinct and must not be used by other calls meanwhile.
+ * status_out (optional, [n]) receives each item's status; the return value is
+ * PP_OK when all succeeded, else the first failing item's status. */
+pp_status pp_propagate_batch(int n, pp_handle* const* handles, const pp_batch_item* items,
+                             int max_threads, pp_status* status_out);
+
 typedef struct {
     size_t n_terms;          /* live terms of O~                                        */
     size_t peak_terms;       /* largest live-term count after any sub-layer             */

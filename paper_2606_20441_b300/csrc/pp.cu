@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -56,10 +58,6 @@ struct NoiseHost {
     uint64_t* d_gx = nullptr;
     uint64_t* d_gz = nullptr;
     int64_t* d_glam = nullptr;
-    std::vector<void*> device_ptrs() const {
-        return {(void*)d_t1, (void*)d_shift, (void*)d_smask, (void*)d_pidx, (void*)d_c2,
-                (void*)d_gx, (void*)d_gz, (void*)d_glam, (void*)d_etab};
-    }
 };
 
 struct Arena {
@@ -76,6 +74,7 @@ struct pp_handle {
     cudaStream_t st = nullptr;
     std::string err;
     int sm_count = 0;
+    int device = 0;
 
     // circuit
     bool have_circuit = false;
@@ -86,8 +85,11 @@ struct pp_handle {
     std::map<int, NoiseHost> noise;
     std::vector<SubLayerDesc> subs;
     std::vector<int> sub_kind;     // growth-estimate class of each sub-layer
-    SubLayerDesc* d_subs = nullptr;
+    SubLayerDesc* d_subs = nullptr;    // inside the table arena
     bool subs_dirty = true;
+    unsigned char* tab_dev = nullptr;  // table arena: descriptors and noise tables
+    size_t tab_cap = 0;
+    std::vector<unsigned char> tab_host;
 
     // memory
     size_t cap = 0;                // terms per arena
@@ -103,8 +105,9 @@ struct pp_handle {
     uint32_t* spill_s = nullptr;
     unsigned long long* spill_ctr = nullptr;   // [NSPILL]
     uint64_t* soff[2] = {nullptr, nullptr};
-    unsigned char* fb_scratch = nullptr;
+    unsigned char* fb_scratch = nullptr;   // global-tier tiles, allocated on first use
     size_t fb_slice = 0;
+    int fb_cap = 0;                        // strings per global-tier tile
     uint64_t* stage = nullptr;     // input staging
     size_t stage_cap = 0;
     __int128* partial = nullptr;
@@ -155,14 +158,6 @@ void dev_free(pp_handle* h, void* p) {
     if (it != h->owned.end()) h->owned.erase(it);
     if (h->opt.free) h->opt.free(p, h->opt.alloc_ctx);
     else cudaFree(p);
-}
-
-template <typename P>
-P* alloc_copy(pp_handle* h, const std::vector<typename std::remove_const<P>::type>& v) {
-    size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(P);
-    P* d = static_cast<P*>(dev_alloc(h, bytes));
-    if (d && !v.empty()) cudaMemcpyAsync((void*)d, v.data(), v.size() * sizeof(P), cudaMemcpyHostToDevice, h->st);
-    return d;
 }
 
 inline int popc_words(const uint64_t* v, int W) {
@@ -311,6 +306,69 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
     (void)layer;
 }
 
+// Copies the sub-layer descriptors and every noise map's tables into the
+// handle's table arena, one host-to-device copy.  The arena only grows, so
+// loading circuits and noise allocates and frees nothing on the device in the
+// steady state (a device free would synchronise every stream on the GPU).
+pp_status upload_tables(pp_handle* h) {
+    auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    std::vector<std::pair<const void*, size_t>> parts;
+    size_t off = 0;
+    std::vector<size_t> offs;
+    auto add = [&](const void* p, size_t bytes) {
+        offs.push_back(off);
+        parts.push_back({p, bytes});
+        off = align(off + std::max<size_t>(bytes, 16));
+    };
+    add(h->subs.data(), sizeof(SubLayerDesc) * h->subs.size());
+    for (auto& kv : h->noise) {
+        NoiseHost& nh = kv.second;
+        add(nh.t1.data(), nh.t1.size() * 8);
+        add(nh.shift.data(), nh.shift.size() * 4);
+        add(nh.smask.data(), nh.smask.size() * 8);
+        add(nh.pidx.data(), nh.pidx.size() * 4);
+        add(nh.c2.data(), nh.c2.size() * 8);
+        add(nh.etab.data(), nh.etab.size() * 8);
+        add(nh.gx.data(), nh.gx.size() * 8);
+        add(nh.gz.data(), nh.gz.size() * 8);
+        add(nh.glam.data(), nh.glam.size() * 8);
+    }
+    if (off > h->tab_cap) {
+        if (h->tab_dev) {
+            cudaStreamSynchronize(h->st);
+            dev_free(h, h->tab_dev);
+            h->tab_dev = nullptr;
+        }
+        h->tab_cap = align(off + off / 2);
+        h->tab_dev = static_cast<unsigned char*>(dev_alloc(h, h->tab_cap));
+        if (!h->tab_dev) {
+            h->tab_cap = 0;
+            return fail(h, PP_ERR_NOMEM, "table arena allocation failed");
+        }
+    }
+    h->tab_host.assign(off, 0);
+    for (size_t k = 0; k < parts.size(); ++k)
+        if (parts[k].second) std::memcpy(h->tab_host.data() + offs[k], parts[k].first, parts[k].second);
+    CK(cudaMemcpyAsync(h->tab_dev, h->tab_host.data(), off, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    size_t k = 0;
+    h->d_subs = reinterpret_cast<SubLayerDesc*>(h->tab_dev + offs[k++]);
+    for (auto& kv : h->noise) {
+        NoiseHost& nh = kv.second;
+        nh.d_t1 = reinterpret_cast<int64_t*>(h->tab_dev + offs[k++]);
+        nh.d_shift = reinterpret_cast<int32_t*>(h->tab_dev + offs[k++]);
+        nh.d_smask = reinterpret_cast<uint64_t*>(h->tab_dev + offs[k++]);
+        nh.d_pidx = reinterpret_cast<int32_t*>(h->tab_dev + offs[k++]);
+        nh.d_c2 = reinterpret_cast<int64_t*>(h->tab_dev + offs[k++]);
+        nh.d_etab = reinterpret_cast<double*>(h->tab_dev + offs[k++]);
+        nh.d_gx = reinterpret_cast<uint64_t*>(h->tab_dev + offs[k++]);
+        nh.d_gz = reinterpret_cast<uint64_t*>(h->tab_dev + offs[k++]);
+        nh.d_glam = reinterpret_cast<int64_t*>(h->tab_dev + offs[k++]);
+    }
+    h->subs_dirty = false;
+    return PP_OK;
+}
+
 pp_status build_plan(pp_handle* h) {
     h->subs.clear();
     h->sub_kind.clear();
@@ -330,13 +388,7 @@ pp_status build_plan(pp_handle* h) {
     }
     h->subs.front().first = 1;
     h->subs.back().final_ = 1;
-    if (h->d_subs) dev_free(h, h->d_subs);
-    h->d_subs = static_cast<SubLayerDesc*>(dev_alloc(h, sizeof(SubLayerDesc) * h->subs.size()));
-    if (!h->d_subs) return fail(h, PP_ERR_NOMEM, "descriptor allocation failed");
-    CK(cudaMemcpyAsync(h->d_subs, h->subs.data(), sizeof(SubLayerDesc) * h->subs.size(),
-                       cudaMemcpyHostToDevice, h->st));
-    h->subs_dirty = false;
-    return PP_OK;
+    return upload_tables(h);
 }
 
 size_t term_bytes(const pp_handle* h) {
@@ -345,14 +397,24 @@ size_t term_bytes(const pp_handle* h) {
 
 int tile_cap(const pp_handle* h) { return h->W == 1 ? kTiers[0].cap1 : kTiers[0].cap2; }
 
-// Bytes of one global-tier slice (int32 indices).
-size_t global_slice_bytes(const pp_handle* h) {
+// Bytes of one global-tier slice of `cap` strings (int32 indices).
+size_t global_slice_bytes(const pp_handle* h, int cap) {
     size_t carved = h->opt.precision == PP_PRECISION_FP32
-        ? (h->W == 1 ? tile_layout_bytes<1, float, int32_t>(kFallbackCap)
-                     : tile_layout_bytes<2, float, int32_t>(kFallbackCap))
-        : (h->W == 1 ? tile_layout_bytes<1, double, int32_t>(kFallbackCap)
-                     : tile_layout_bytes<2, double, int32_t>(kFallbackCap));
+        ? (h->W == 1 ? tile_layout_bytes<1, float, int32_t>(cap) : tile_layout_bytes<2, float, int32_t>(cap))
+        : (h->W == 1 ? tile_layout_bytes<1, double, int32_t>(cap) : tile_layout_bytes<2, double, int32_t>(cap));
     return (carved + 255) & ~(size_t)255;
+}
+
+// The global tier's tiles: kFallbackCTAs slices, each for up to a quarter of
+// the handle's capacity (at most kFallbackCap strings), allocated the first
+// time a bucket reaches that tier.
+pp_status ensure_global_tier(pp_handle* h) {
+    if (h->fb_scratch) return PP_OK;
+    h->fb_cap = (int)std::min<size_t>(kFallbackCap, std::max<size_t>(4096, h->cap / 4));
+    h->fb_slice = global_slice_bytes(h, h->fb_cap);
+    h->fb_scratch = static_cast<unsigned char*>(dev_alloc(h, h->fb_slice * kFallbackCTAs));
+    if (!h->fb_scratch) return fail(h, PP_ERR_NOMEM, "global-tier scratch allocation failed");
+    return PP_OK;
 }
 
 pp_status alloc_arena(pp_handle* h, Arena* a, size_t cap) {
@@ -397,11 +459,7 @@ pp_status ensure_memory(pp_handle* h) {
         if (!(h->pass_list[k] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap))))
             return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * 4096));
-    h->fb_slice = global_slice_bytes(h);
-    if (h->fb_slice == 0) return fail(h, PP_ERR_CUDA, "internal: global tile layout exceeds its slice");
-    h->fb_scratch = static_cast<unsigned char*>(dev_alloc(h, h->fb_slice * kFallbackCTAs));
-    if (!h->spill_b || !h->spill_s || !h->counters || !h->delta ||
-        !h->partial || !h->fb_scratch)
+    if (!h->spill_b || !h->spill_s || !h->counters || !h->delta || !h->partial)
         return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     return PP_OK;
 }
@@ -416,11 +474,11 @@ uint32_t pow2_at_least(double v, uint32_t cap) {
 template <int W, typename T, int NT>
 cudaError_t launch_smem_tier(pp_handle* h, const StepParams& p, int cap, uint32_t n_items) {
     const size_t smem = tile_layout_bytes<W, T, int16_t>((size_t)cap);
-    static size_t attr_set = 0;
-    if (attr_set < smem) {
+    static std::atomic<size_t> attr_set(0);   // shared by the threads of pp_propagate_batch
+    if (attr_set.load() < smem) {
         cudaError_t e = cudaFuncSetAttribute(k_process<W, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = smem;
+        attr_set.store(smem);
     }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T, NT>, NT, smem);
@@ -437,12 +495,12 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t
     switch (tier) {
         case 0: {
             const size_t smem = warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS;
-            static size_t attr_set = 0;
-            if (attr_set < smem) {
+            static std::atomic<size_t> attr_set(0);
+            if (attr_set.load() < smem) {
                 cudaError_t e = cudaFuncSetAttribute(k_process_warp<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)smem);
                 if (e != cudaSuccess) return e;
-                attr_set = smem;
+                attr_set.store(smem);
             }
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process_warp<W, T>, kTiers[0].threads, smem);
@@ -457,7 +515,7 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t
         default: {
             uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)kFallbackCTAs);
             k_process_global<W, T><<<grid, kTiers[kGlobalTier].threads, 0, h->st>>>(p, h->fb_scratch, h->fb_slice,
-                                                                                  kFallbackCap);
+                                                                                  h->fb_cap);
             return cudaGetLastError();
         }
     }
@@ -594,6 +652,7 @@ pp_status pp_create(const pp_options* opt, int n_qubits, pp_handle** out) {
     h->n = n_qubits;
     h->W = (n_qubits + 63) / 64;
     h->st = static_cast<cudaStream_t>(h->opt.cuda_stream);
+    h->device = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -601,6 +660,7 @@ pp_status pp_create(const pp_options* opt, int n_qubits, pp_handle** out) {
         delete h;
         return PP_ERR_CUDA;
     }
+    h->device = dev;
     *out = h;
     return PP_OK;
 }
@@ -656,10 +716,6 @@ pp_status pp_load_circuit(pp_handle* h, size_t n_gates, const uint64_t* rx, cons
     h->theta.assign(theta, theta + n_gates);
     h->layer_of.assign(layer_of, layer_of + n_gates);
     h->n_layers = n_layers;
-    for (auto& kv : h->noise) {
-        NoiseHost& nh = kv.second;
-        for (void* p : nh.device_ptrs()) dev_free(h, p);
-    }
     h->noise.clear();
     h->have_circuit = true;
     h->have_result = false;
@@ -760,17 +816,7 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
         nh.smask[(size_t)c * W + (a >> 6)] |= 1ull << (a & 63);
         nh.pidx[(size_t)c * n + a] = (int32_t)i;
     }
-    auto old = h->noise.find(layer);
-    if (old != h->noise.end()) {
-        NoiseHost& o = old->second;
-        for (void* p : o.device_ptrs()) dev_free(h, p);
-        h->noise.erase(old);
-    }
-    nh.d_t1 = alloc_copy<int64_t>(h, nh.t1);
-    nh.d_shift = alloc_copy<int32_t>(h, nh.shift);
-    nh.d_smask = alloc_copy<uint64_t>(h, nh.smask);
-    nh.d_pidx = alloc_copy<int32_t>(h, nh.pidx);
-    nh.d_c2 = alloc_copy<int64_t>(h, nh.c2);
+    h->noise.erase(layer);
     // factor tables: entry (i, b) = exp(+-2 * b * 2^(8i - 56)), evaluated in extended
     // precision and rounded once to double
     nh.etab.assign(8 * 256, 1.0);
@@ -779,14 +825,6 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
             long double e = std::ldexp((long double)b, 8 * i - FIX_SHIFT) * 2.0L;
             nh.etab[256 * i + b] = (double)std::exp(mode == PP_NOISE_INVERSE ? e : -e);
         }
-    nh.d_etab = alloc_copy<double>(h, nh.etab);
-    nh.d_gx = alloc_copy<uint64_t>(h, nh.gx);
-    nh.d_gz = alloc_copy<uint64_t>(h, nh.gz);
-    nh.d_glam = alloc_copy<int64_t>(h, nh.glam);
-    if (!nh.d_t1 || !nh.d_shift || !nh.d_smask || !nh.d_pidx || !nh.d_c2 || !nh.d_gx || !nh.d_gz ||
-        !nh.d_glam || !nh.d_etab)
-        return fail(h, PP_ERR_NOMEM, "noise table allocation failed");
-    if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, PP_ERR_CUDA, "noise upload failed");
     h->noise[layer] = std::move(nh);
     h->have_result = false;
     h->subs_dirty = true;
@@ -958,7 +996,8 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
             p.out_list = tier < kGlobalTier ? h->pass_list[tier] : nullptr;
             p.work_ctr = CTR_WORK + tier;
             p.defer_ctr = CTR_DEFER + (tier < kGlobalTier ? tier : 0);
-            p.max_load = (uint32_t)(tier_cap(h, tier) * 3 / 4);
+            if (tier == kGlobalTier && (st = ensure_global_tier(h)) != PP_OK) return st;
+            p.max_load = (uint32_t)((tier == kGlobalTier ? h->fb_cap : tier_cap(h, tier)) * 3 / 4);
             CK(cudaEventRecord(scope.ev[0], h->st));
             CK(dispatch_process(h, p, tier, n_items, &launches));
             CK(cudaEventRecord(scope.ev[1], h->st));
@@ -973,7 +1012,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         stats.fallback_buckets += (int)passed[kGlobalTier - 1];
         if (ctr[CTR_ERR_FALLBACK])
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s,
-                        kFallbackCap);
+                        h->fb_cap);
         if (ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap)
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
                         "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap,
@@ -1096,6 +1135,39 @@ pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, do
         if (c) c[k] = hc[i];
     }
     return PP_OK;
+}
+
+pp_status pp_propagate_batch(int n, pp_handle* const* handles, const pp_batch_item* items, int max_threads,
+                             pp_status* status_out) {
+    if (n < 0 || (n > 0 && (!handles || !items))) return PP_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!handles[i]) return PP_ERR_ARG;
+    std::vector<pp_status> st(n, PP_OK);
+    std::atomic<int> next(0);
+    auto worker = [&]() {
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= n) return;
+            pp_handle* h = handles[i];
+            if (cudaSetDevice(h->device) != cudaSuccess) {
+                cudaGetLastError();
+                st[i] = PP_ERR_CUDA;
+                continue;
+            }
+            const pp_batch_item& it = items[i];
+            st[i] = pp_propagate(h, it.n_terms, it.ox, it.oz, it.oc, it.eps, it.w_max);
+        }
+    };
+    const int nt = std::max(1, std::min(n, max_threads > 0 ? max_threads : 16));
+    std::vector<std::thread> pool;
+    for (int k = 0; k < nt; ++k) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    pp_status first = PP_OK;
+    for (int i = 0; i < n; ++i) {
+        if (status_out) status_out[i] = st[i];
+        if (first == PP_OK && st[i] != PP_OK) first = st[i];
+    }
+    return first;
 }
 
 pp_status pp_get_stats(const pp_handle* h, pp_stats* out) {

@@ -54,6 +54,15 @@ class pp_stats(ctypes.Structure):
                 ("bytes_per_string", ctypes.c_double)]
 
 
+class pp_batch_item(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_size_t),
+                ("ox", ctypes.c_void_p),
+                ("oz", ctypes.c_void_p),
+                ("oc", ctypes.c_void_p),
+                ("eps", ctypes.c_double),
+                ("w_max", ctypes.c_int)]
+
+
 class PPError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -62,7 +71,7 @@ class PPError(RuntimeError):
 
 EXPORTED = ["pp_default_options", "pp_create", "pp_destroy", "pp_load_circuit", "pp_load_noise",
             "pp_propagate", "pp_expect", "pp_export_terms", "pp_get_stats", "pp_last_error",
-            "pp_expect_noalloc"]
+            "pp_expect_noalloc", "pp_propagate_batch"]
 NOALLOC_MAX_TERMS = 1 << 27
 
 _lib = None
@@ -90,6 +99,8 @@ def load_library(path: str = LIB_PATH):
     L.pp_last_error.argtypes = [vp]
     L.pp_last_error.restype = ctypes.c_char_p
     L.pp_expect_noalloc.argtypes = [ctypes.c_int, sz, vp, vp, vp, vp]
+    L.pp_propagate_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(pp_batch_item),
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     for f in EXPORTED:
         if f not in ("pp_default_options", "pp_last_error"):
             getattr(L, f).restype = ctypes.c_int
@@ -106,6 +117,7 @@ class Handle:
 
     def __init__(self, n_qubits: int, precision: int = PRECISION_FP64, max_terms: int = 0,
                  torch_memory: bool = False, stream: Optional[int] = None):
+        """stream: a cudaStream_t (as int) to run on; None = the legacy default stream."""
         self.L = load_library()
         self.n_qubits = n_qubits
         self.W = inputs.n_words(n_qubits)
@@ -139,6 +151,9 @@ class Handle:
     def _check(self, status: int):
         if status != PP_OK:
             raise PPError(status, self.L.pp_last_error(self.h).decode())
+
+    def last_error(self) -> str:
+        return self.L.pp_last_error(self.h).decode()
 
     def close(self):
         if getattr(self, "h", None):
@@ -198,7 +213,10 @@ class Handle:
 
     # convenience: a whole Instance
     def load_instance(self, inst: "inputs.Instance"):
-        assert inst.n_qubits == self.n_qubits
+        """A handle for n qubits runs any instance on at most n qubits with the
+        same number of mask words."""
+        if inst.n_qubits > self.n_qubits or inst.W != self.W:
+            raise ValueError("instance on %d qubits does not fit a handle for %d" % (inst.n_qubits, self.n_qubits))
         self.pp_load_circuit(inst.gate_x, inst.gate_z, inst.theta, inst.layer_of, inst.n_layers)
         for m in inst.noise:
             self.pp_load_noise(m.layer, m.ex, m.ez, m.lam, m.mode)
@@ -208,6 +226,27 @@ class Handle:
         self.pp_propagate(inst.obs_x, inst.obs_z, inst.obs_c,
                           inst.eps if eps is None else eps,
                           inst.w_max if w_max is None else w_max)
+
+
+def pp_propagate_batch(handles, instances, max_threads: int = 16, eps=None, w_max=None):
+    """pp_propagate for many handles at once (each handle on its own stream);
+    returns the per-item status list."""
+    L = load_library()
+    n = len(handles)
+    keep = []
+    items = (pp_batch_item * max(n, 1))()
+    for k, (h, inst) in enumerate(zip(handles, instances)):
+        ox = np.ascontiguousarray(inst.obs_x, dtype=np.uint64)
+        oz = np.ascontiguousarray(inst.obs_z, dtype=np.uint64)
+        oc = np.ascontiguousarray(inst.obs_c, dtype=np.float64)
+        keep += [ox, oz, oc]
+        items[k] = pp_batch_item(len(oc), _p(ox).value, _p(oz).value, _p(oc).value,
+                                 float(inst.eps if eps is None else eps),
+                                 int(inst.w_max if w_max is None else w_max))
+    hs = (ctypes.c_void_p * max(n, 1))(*[h.h.value for h in handles])
+    st = (ctypes.c_int * max(n, 1))()
+    L.pp_propagate_batch(n, hs, items, int(max_threads), st)
+    return [st[k] for k in range(n)]
 
 
 def pp_expect_noalloc(n_qubits: int, n_terms: int, x_dev: int, c_dev: int, value_dev: int,

@@ -1,0 +1,55 @@
+"""Batched and served propagations on the GPU: every result equals the same
+request run alone (same precision), bit for bit on the exact expectation."""
+import numpy as np
+import pytest
+
+from paper_2606_20441_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pp():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2606_20441_b300 import build, pp as ppmod
+    build.build()
+    return ppmod
+
+
+def alone(pp, inst, precision):
+    r = pp.propagate(inst, precision=precision, max_terms=20_000_000, export=False)
+    return r.expect, r.stats.n_terms
+
+
+def test_batch_matches_single_runs(pp):
+    import torch
+    insts = inputs.workload_batch64(count=12, eps=1e-4, w_max=8)
+    streams = [torch.cuda.Stream() for _ in insts]
+    hs = [pp.Handle(i.n_qubits, precision=32, max_terms=20_000_000, stream=s.cuda_stream)
+          for i, s in zip(insts, streams)]
+    for h, i in zip(hs, insts):
+        h.load_instance(i)
+    st = pp.pp_propagate_batch(hs, insts, max_threads=6)
+    assert all(s == pp.PP_OK for s in st), [(s, h.last_error()) for s, h in zip(st, hs)]
+    for h, i in zip(hs, insts):
+        e_ref, n_ref = alone(pp, i, 32)
+        assert h.pp_get_stats().n_terms == n_ref
+        assert h.pp_expect() == e_ref
+        h.close()
+
+
+def test_served_results_equal_alone(pp):
+    from paper_2606_20441_b300 import serving
+    reqs = inputs.workload_serving(count=16, rate_hz=200.0, side_hi=7, steps_hi=10,
+                                   eps_set=(1e-4, 1e-5), w_max=8)
+    ex = serving.GpuExecutor(n_workers=4, hbm_budget_bytes=16e9, precision=32)
+    try:
+        out = serving.Server(ex, n_workers=4).serve(reqs)
+    finally:
+        ex.close()
+    assert all(o.status == pp.PP_OK for o in out), [(o.rid, o.status) for o in out]
+    for o, r in zip(out, sorted(reqs, key=lambda r: r.rid)):
+        e_ref, n_ref = alone(pp, r.instance, 32)
+        assert o.terms == n_ref
+        assert o.expect == e_ref

@@ -1,0 +1,50 @@
+"""Host-side scheduling of the serving loop (no GPU): FIFO admission onto a
+fixed set of workers, concurrency bounded by the workers, latency bookkeeping."""
+import threading
+import time
+
+from paper_2606_20441_b300 import inputs, serving
+
+
+class FakeExecutor:
+    def __init__(self, service_s=0.02):
+        self.service_s = service_s
+        self.active = 0
+        self.max_active = 0
+        self.lock = threading.Lock()
+        self.order = []
+
+    def run(self, worker, inst):
+        with self.lock:
+            self.active += 1
+            self.max_active = max(self.max_active, self.active)
+            self.order.append(inst.name)
+        time.sleep(self.service_s)
+        with self.lock:
+            self.active -= 1
+        return 0, float(len(inst.name)), 10.0, 1
+
+
+def test_fifo_bounded_concurrency_and_latency():
+    reqs = inputs.workload_serving(count=12, rate_hz=400.0, side_hi=5, steps_hi=6)
+    ex = FakeExecutor()
+    out = serving.Server(ex, n_workers=3).serve(reqs)
+    assert [o.rid for o in out] == list(range(12))
+    assert ex.max_active <= 3
+    assert ex.order == [r.instance.name for r in sorted(reqs, key=lambda r: r.arrival_s)]
+    for o in out:
+        assert o.start_s >= o.arrival_s - 1e-3
+        assert o.latency_s >= ex.service_s * 0.9
+    s = serving.summarize(out)
+    assert s["served"] == 12 and s["failed"] == 0 and s["p99_ms"] >= s["p50_ms"]
+
+
+def test_failures_are_reported_not_retried():
+    class Failing(FakeExecutor):
+        def run(self, worker, inst):
+            super().run(worker, inst)
+            return 4, None, 0.0, 0
+    reqs = inputs.workload_serving(count=4, rate_hz=1000.0, side_hi=4, steps_hi=5)
+    out = serving.Server(Failing(0.001), n_workers=2).serve(reqs)
+    s = serving.summarize(out)
+    assert s["failed"] == 4 and s["served"] == 0
