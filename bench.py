@@ -321,65 +321,77 @@ def ours_arm(args, rank, world, local_rank):
 def pool_arm(args, rank, world, local_rank):
     """Many independent instances on one GPU: the 64-instance batch (all
     requests present at once) or a Poisson request stream, through the serving
-    loop's workers (each worker: own CUDA stream, own handles, a share of the
-    HBM budget).  Also times the same instances one after another on a single
-    FP64 handle -- the plain single-instance path -- for comparison."""
+    loop (small-share workers plus one large-share worker for requests that
+    outgrow a small share; each worker on its own CUDA stream with its own
+    handles; the plan autotuner learning per workload class on live traffic).
+    The same instances are then run one after another through the plain
+    single-instance FP64 path, which gives both the throughput to compare with
+    and the FP32 form's error against FP64 on every instance."""
     import torch
-    from paper_2606_20441_b300 import build, pp, serving
+    from paper_2606_20441_b300 import autotune, build, pp, serving
     torch.cuda.set_device(local_rank)
     build.build()
+    eps, w_max = 1e-4, 8
     if args.workload == "batch64":
-        insts = inputs.workload_batch64(eps=1e-5, w_max=10)
+        insts = inputs.workload_batch64(eps=eps, w_max=w_max)
         reqs = [inputs.Request(i, 0.0, inst) for i, inst in enumerate(insts)]
-        cfg = {"workload": "batch64_eps1e-05_wmax10", "instances": len(insts),
-               "lattices": "4x4..8x8", "trotter_steps": "5-25", "coefficients": "fp%d" % args.precision,
-               "parallelism": "replicas", "workers": args.workers, "l2": "working set larger than L2"}
+        cfg = {"workload": "batch64_eps%g_wmax%d" % (eps, w_max), "instances": len(insts),
+               "lattices": "4x4..8x8", "trotter_steps": "5-25"}
     else:
-        reqs = inputs.workload_serving(count=args.requests, rate_hz=args.rate, eps_set=(1e-4, 1e-5), w_max=10)
+        reqs = inputs.workload_serving(count=args.requests, rate_hz=args.rate, eps_set=(eps,), w_max=w_max)
         insts = [r.instance for r in reqs]
-        cfg = {"workload": "serving_poisson%gHz_eps1e-4..1e-5_wmax10" % args.rate, "requests": len(reqs),
-               "lattices": "4x4..10x10", "trotter_steps": "5-30", "coefficients": "fp%d" % args.precision,
-               "parallelism": "replicas", "workers": args.workers, "l2": "working set larger than L2"}
+        cfg = {"workload": "serving_poisson%gHz_eps%g_wmax%d" % (args.rate, eps, w_max), "requests": len(reqs),
+               "lattices": "4x4..10x10", "trotter_steps": "5-30"}
+    cfg.update({"coefficients": "fp%d" % args.precision, "parallelism": "replicas",
+                "workers": "%d small + 1 large" % args.workers, "l2": "working set larger than L2"})
     budget = 0.6 * torch.cuda.mem_get_info()[0]
-    ex = serving.GpuExecutor(n_workers=args.workers, hbm_budget_bytes=budget, precision=args.precision)
-    # warm-up: every worker runs a small request
-    small = inputs.workload_batch64(count=args.workers, eps=1e-4, w_max=6)
-    serving.Server(ex, n_workers=args.workers).serve([inputs.Request(i, 0.0, x) for i, x in enumerate(small)])
+    tuner = autotune.Tuner()
+    ex = serving.GpuExecutor(n_small=args.workers, hbm_budget_bytes=budget, precision=args.precision,
+                             n_large=1, large_fraction=0.5, tuner=tuner)
+    # warm-up: every worker runs a small request (not seen by the tuner)
+    ex.tuner = None
+    small = inputs.workload_batch64(count=args.workers + 1, eps=1e-3, w_max=6)
+    serving.Server(ex, n_workers=args.workers, n_large=1).serve(
+        [inputs.Request(i, 0.0, x) for i, x in enumerate(small)])
+    ex.tuner = tuner
     torch.cuda.synchronize()
-    out = serving.Server(ex, n_workers=args.workers).serve(reqs)
+    out = serving.Server(ex, n_workers=args.workers, n_large=1).serve(reqs)
     torch.cuda.synchronize()
     ex.close()
     summ = serving.summarize(out)
     # the plain single-instance FP64 path over the same instances, one at a time
-    single_upd, single_s = 0.0, 0.0
+    single_upd, single_s, max_err, n_cmp = 0.0, 0.0, 0.0, 0
     if not args.no_single:
-        h1 = pp.Handle(64, precision=64, max_terms=int(budget / 2.6 / 24))
-        h2 = None
-        for inst in insts:
-            h = h1
-            if inst.W == 2:
-                h2 = h2 or pp.Handle(128, precision=64, max_terms=int(budget / 2.6 / 40 / 2))
-                h = h2
-            h.load_instance(inst)
+        hs = {1: pp.Handle(64, precision=64, max_terms=int(budget / 2.6 / 24 / 2)),
+              2: pp.Handle(128, precision=64, max_terms=int(budget / 2.6 / 40 / 2))}
+        by_rid = {o.rid: o for o in out}
+        for r in reqs:
+            h = hs[r.instance.W]
+            h.load_instance(r.instance)
             t = time.perf_counter()
             try:
-                h.run_instance(inst)
-                h.pp_expect()
+                h.run_instance(r.instance)
+                e64 = h.pp_expect()
                 single_upd += h.pp_get_stats().updates
+                single_s += time.perf_counter() - t
+                o = by_rid[r.rid]
+                if o.status == pp.PP_OK:
+                    max_err = max(max_err, abs(o.expect - e64))
+                    n_cmp += 1
             except pp.PPError:
-                pass
-            single_s += time.perf_counter() - t
-        h1.close()
-        if h2:
-            h2.close()
+                single_s += time.perf_counter() - t
+        for h in hs.values():
+            h.close()
     if rank != 0:
         return
     line = {"metric": METRIC, "value": summ["updates_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": summ["span_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f%d" % args.precision, "data": "synthetic",
             "config": cfg, "served": summ["served"], "failed": summ["failed"],
-            "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
-            "single_instance_fp64_updates_per_s": single_upd / single_s if single_s > 0 else None}
+            "escalated": summ["escalated"], "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
+            "single_instance_fp64_updates_per_s": single_upd / single_s if single_s > 0 else None,
+            "fp32_vs_fp64_max_abs_err": max_err if n_cmp else None, "compared": n_cmp,
+            "tuned": {k: list(tuner.best(k)) for k in sorted(tuner.samples)}}
     print(json.dumps(line), flush=True)
 
 
@@ -396,8 +408,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--workers", type=int, default=16)
-    ap.add_argument("--requests", type=int, default=400)
-    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--requests", type=int, default=150)
+    ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--no-single", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -172,6 +172,29 @@ pp_status pp_get_stats(const pp_handle* h, pp_stats* out);
 /* Description of the last failure on this handle ("" if none).  Valid until the next call. */
 const char* pp_last_error(const pp_handle* h);
 
+/* Plan tuning.  A propagation's result does not depend on it: every plan
+ * reproduces gate-by-gate propagation with per-gate truncation exactly
+ * (Sec. I, Eq. evolve_gate, truncation after every gate); only the run time
+ * does.
+ *   max_fused_gates  commuting gates fused into one sub-layer (one pass over
+ *                    the strings), 1..64*W; 0 = library default (16).  More
+ *                    gates mean fewer passes but larger orbits per bucket.
+ *   bucket_headroom  buckets are sized so that a bucket's strings times the
+ *                    sub-layer's observed growth, times this factor, fill one
+ *                    warp tile; in [1, 16]; 0 = library default (1.6).  Larger
+ *                    values mean more, emptier buckets.
+ * pp_set_tuning copies *t and takes effect at the next pp_propagate.
+ * Errors: PP_ERR_ARG (NULL pointer, value out of range; the handle keeps its
+ * previous tuning).  pp_get_tuning writes the values in effect (defaults
+ * resolved). */
+typedef struct {
+    int max_fused_gates;
+    double bucket_headroom;
+} pp_tuning;
+
+pp_status pp_set_tuning(pp_handle* h, const pp_tuning* t);
+pp_status pp_get_tuning(const pp_handle* h, pp_tuning* t);
+
 /* Largest term count pp_expect_noalloc accepts (2^27). */
 #define PP_NOALLOC_MAX_TERMS ((size_t)134217728)
 

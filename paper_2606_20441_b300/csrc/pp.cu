@@ -70,6 +70,7 @@ struct Arena {
 
 struct pp_handle {
     pp_options opt;
+    pp_tuning tune{0, 0.0};   // zeros select the library defaults
     int n = 0, W = 1;
     cudaStream_t st = nullptr;
     std::string err;
@@ -220,9 +221,14 @@ int sig_kind(const SubLayerDesc& d) {
 // 2^(acting gates) strings, so smaller sub-layers keep orbits small enough for
 // the one-warp tiles at the price of more passes over the strings.
 int max_fused_gates(const pp_handle* h) {
-    int m = std::min(16, 64 * h->W);   // measured best trade-off on the 6x6 and 7x8 TFIM workloads
-    if (const char* e = getenv("PP_MAX_FUSED_GATES")) m = std::max(1, std::min(m, atoi(e)));
-    return m;
+    // default: the measured best trade-off on the 6x6 and 7x8 TFIM workloads
+    int m = h->tune.max_fused_gates > 0 ? h->tune.max_fused_gates : 16;
+    if (const char* e = getenv("PP_MAX_FUSED_GATES")) m = atoi(e);
+    return std::max(1, std::min(m, 64 * h->W));
+}
+
+double bucket_headroom(const pp_handle* h) {
+    return h->tune.bucket_headroom > 0.0 ? h->tune.bucket_headroom : 1.6;
 }
 
 // Splits a layer's gates (listed order) into fused sub-layers.
@@ -676,6 +682,25 @@ pp_status pp_destroy(pp_handle* h) {
 
 const char* pp_last_error(const pp_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
+pp_status pp_set_tuning(pp_handle* h, const pp_tuning* t) {
+    if (!h || !t) return PP_ERR_ARG;
+    h->err.clear();
+    if (t->max_fused_gates < 0 || t->max_fused_gates > 64 * h->W)
+        return fail(h, PP_ERR_ARG, "max_fused_gates must be 0 (default) or 1..64*W");
+    if (t->bucket_headroom != 0.0 && !(t->bucket_headroom >= 1.0 && t->bucket_headroom <= 16.0))
+        return fail(h, PP_ERR_ARG, "bucket_headroom must be 0 (default) or in [1, 16]");
+    if (t->max_fused_gates != h->tune.max_fused_gates) h->subs_dirty = true;
+    h->tune = *t;
+    return PP_OK;
+}
+
+pp_status pp_get_tuning(const pp_handle* h, pp_tuning* t) {
+    if (!h || !t) return PP_ERR_ARG;
+    t->max_fused_gates = max_fused_gates(h);
+    t->bucket_headroom = bucket_headroom(h);
+    return PP_OK;
+}
+
 pp_status pp_load_circuit(pp_handle* h, size_t n_gates, const uint64_t* rx, const uint64_t* rz,
                           const double* theta, const int32_t* layer_of, int n_layers) {
     if (!h) return PP_ERR_ARG;
@@ -889,9 +914,10 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         return it == growth.end() ? 3.0 : it->second;
     };
     // buckets for sub-layer s holding about n strings: its tile must also hold
-    // the strings the sub-layer creates, so aim at tcap / (1.6 * growth)
+    // the strings the sub-layer creates, so aim at tcap / (headroom * growth)
+    const double headroom = bucket_headroom(h);
     auto buckets_for = [&](int s, double n) {
-        double per = (double)tcap / (1.6 * std::max(1.0, growth_of(s)));
+        double per = (double)tcap / (headroom * std::max(1.0, growth_of(s)));
         per = std::max(per, 16.0);
         return pow2_at_least(n / per, h->fill_cap);
     };

@@ -63,6 +63,11 @@ class pp_batch_item(ctypes.Structure):
                 ("w_max", ctypes.c_int)]
 
 
+class pp_tuning(ctypes.Structure):
+    _fields_ = [("max_fused_gates", ctypes.c_int),
+                ("bucket_headroom", ctypes.c_double)]
+
+
 class PPError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -71,7 +76,7 @@ class PPError(RuntimeError):
 
 EXPORTED = ["pp_default_options", "pp_create", "pp_destroy", "pp_load_circuit", "pp_load_noise",
             "pp_propagate", "pp_expect", "pp_export_terms", "pp_get_stats", "pp_last_error",
-            "pp_expect_noalloc", "pp_propagate_batch"]
+            "pp_expect_noalloc", "pp_propagate_batch", "pp_set_tuning", "pp_get_tuning"]
 NOALLOC_MAX_TERMS = 1 << 27
 
 _lib = None
@@ -101,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     L.pp_expect_noalloc.argtypes = [ctypes.c_int, sz, vp, vp, vp, vp]
     L.pp_propagate_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(pp_batch_item),
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.pp_set_tuning.argtypes = [vp, ctypes.POINTER(pp_tuning)]
+    L.pp_get_tuning.argtypes = [vp, ctypes.POINTER(pp_tuning)]
     for f in EXPORTED:
         if f not in ("pp_default_options", "pp_last_error"):
             getattr(L, f).restype = ctypes.c_int
@@ -210,6 +217,15 @@ class Handle:
         s = pp_stats()
         self._check(self.L.pp_get_stats(self.h, ctypes.byref(s)))
         return s
+
+    def pp_set_tuning(self, max_fused_gates: int = 0, bucket_headroom: float = 0.0):
+        t = pp_tuning(int(max_fused_gates), float(bucket_headroom))
+        self._check(self.L.pp_set_tuning(self.h, ctypes.byref(t)))
+
+    def pp_get_tuning(self):
+        t = pp_tuning()
+        self._check(self.L.pp_get_tuning(self.h, ctypes.byref(t)))
+        return t.max_fused_gates, t.bucket_headroom
 
     # convenience: a whole Instance
     def load_instance(self, inst: "inputs.Instance"):

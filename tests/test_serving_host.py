@@ -48,3 +48,45 @@ def test_failures_are_reported_not_retried():
     out = serving.Server(Failing(0.001), n_workers=2).serve(reqs)
     s = serving.summarize(out)
     assert s["failed"] == 4 and s["served"] == 0
+
+
+def test_capacity_failures_escalate_to_large_workers():
+    """A request that outgrows a small worker's share is re-admitted to the
+    large workers with its original arrival time and served there."""
+    class Shares(FakeExecutor):
+        def run(self, worker, inst):
+            super().run(worker, inst)
+            big = inst.n_qubits > 20
+            if big and worker < 2:
+                return serving.PP_ERR_CAPACITY, None, 0.0, 0
+            return 0, 1.0, 5.0, 1
+    reqs = inputs.workload_serving(count=10, rate_hz=500.0, side_hi=6, steps_hi=5)
+    ex = Shares(0.002)
+    out = serving.Server(ex, n_workers=2, n_large=1).serve(reqs)
+    assert [o.rid for o in out] == list(range(10))
+    by_rid = {r.rid: r for r in reqs}
+    for o in out:
+        big = by_rid[o.rid].instance.n_qubits > 20
+        assert o.status == 0
+        assert o.arrival_s <= o.start_s + 1e-3
+        if big:
+            assert o.worker == 2
+        if o.escalated:
+            assert big
+    assert any(by_rid[o.rid].instance.n_qubits > 20 for o in out)
+    s = serving.summarize(out)
+    assert s["served"] == 10 and s["failed"] == 0
+
+
+def test_large_worker_failures_are_final():
+    class AlwaysFull(FakeExecutor):
+        def run(self, worker, inst):
+            super().run(worker, inst)
+            return serving.PP_ERR_CAPACITY, None, 0.0, 0
+    reqs = inputs.workload_serving(count=5, rate_hz=1000.0, side_hi=4, steps_hi=5)
+    ex = AlwaysFull(0.001)
+    out = serving.Server(ex, n_workers=2, n_large=1).serve(reqs)
+    assert len(out) == 5 and all(o.status == serving.PP_ERR_CAPACITY for o in out)
+    assert all(o.worker == 2 for o in out)
+    # each request ran at most once on a small worker, then once on the large one
+    assert len(ex.order) <= 10
