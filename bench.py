@@ -320,13 +320,13 @@ def ours_arm(args, rank, world, local_rank):
 
 def pool_arm(args, rank, world, local_rank):
     """Many independent instances on one GPU: the 64-instance batch (all
-    requests present at once) or a Poisson request stream, through the serving
-    loop (small-share workers plus one large-share worker for requests that
-    outgrow a small share; each worker on its own CUDA stream with its own
-    handles; the plan autotuner learning per workload class on live traffic).
-    The same instances are then run one after another through the plain
-    single-instance FP64 path, which gives both the throughput to compare with
-    and the FP32 form's error against FP64 on every instance."""
+    requests present at once, largest first) or a Poisson request stream,
+    through the serving loop (small-share workers plus large-share workers for
+    requests that outgrow a small share; each worker on its own CUDA stream
+    with its own handle; the plan autotuner learning per workload class on live
+    traffic).  The same instances are then run one after another through the
+    plain single-instance path in FP64 (the throughput to compare with, and the
+    FP32 form's error against FP64 on every instance) and in FP32."""
     import torch
     from paper_2606_20441_b300 import autotune, build, pp, serving
     torch.cuda.set_device(local_rank)
@@ -334,7 +334,7 @@ def pool_arm(args, rank, world, local_rank):
     eps, w_max = 1e-4, 8
     if args.workload == "batch64":
         insts = inputs.workload_batch64(eps=eps, w_max=w_max)
-        reqs = [inputs.Request(i, 0.0, inst) for i, inst in enumerate(insts)]
+        reqs = serving.batch_order([inputs.Request(i, 0.0, inst) for i, inst in enumerate(insts)])
         cfg = {"workload": "batch64_eps%g_wmax%d" % (eps, w_max), "instances": len(insts),
                "lattices": "4x4..8x8", "trotter_steps": "5-25"}
     else:
@@ -342,46 +342,56 @@ def pool_arm(args, rank, world, local_rank):
         insts = [r.instance for r in reqs]
         cfg = {"workload": "serving_poisson%gHz_eps%g_wmax%d" % (args.rate, eps, w_max), "requests": len(reqs),
                "lattices": "4x4..10x10", "trotter_steps": "5-30"}
+    n_large = 2
     cfg.update({"coefficients": "fp%d" % args.precision, "parallelism": "replicas",
-                "workers": "%d small + 1 large" % args.workers, "l2": "working set larger than L2"})
+                "workers": "%d small + %d large" % (args.workers, n_large), "l2": "working set larger than L2"})
     budget = 0.6 * torch.cuda.mem_get_info()[0]
     tuner = autotune.Tuner()
     ex = serving.GpuExecutor(n_small=args.workers, hbm_budget_bytes=budget, precision=args.precision,
-                             n_large=1, large_fraction=0.5, tuner=tuner)
+                             n_large=n_large, large_fraction=0.3, tuner=tuner)
     # warm-up: every worker runs a small request (not seen by the tuner)
     ex.tuner = None
-    small = inputs.workload_batch64(count=args.workers + 1, eps=1e-3, w_max=6)
-    serving.Server(ex, n_workers=args.workers, n_large=1).serve(
+    small = inputs.workload_batch64(count=args.workers + n_large, eps=1e-3, w_max=6)
+    serving.Server(ex, n_workers=args.workers, n_large=n_large).serve(
         [inputs.Request(i, 0.0, x) for i, x in enumerate(small)])
     ex.tuner = tuner
     torch.cuda.synchronize()
-    out = serving.Server(ex, n_workers=args.workers, n_large=1).serve(reqs)
+    out = serving.Server(ex, n_workers=args.workers, n_large=n_large, route_key=autotune.class_key).serve(reqs)
     torch.cuda.synchronize()
     ex.close()
+    torch.cuda.empty_cache()   # the workers' memory went back to torch's cache
     summ = serving.summarize(out)
-    # the plain single-instance FP64 path over the same instances, one at a time
-    single_upd, single_s, max_err, n_cmp = 0.0, 0.0, 0.0, 0
-    if not args.no_single:
-        hs = {1: pp.Handle(64, precision=64, max_terms=int(budget / 2.6 / 24 / 2)),
-              2: pp.Handle(128, precision=64, max_terms=int(budget / 2.6 / 40 / 2))}
-        by_rid = {o.rid: o for o in out}
+    # the plain single-instance path over the same instances, one at a time:
+    # FP64 (the comparison point, and the FP32 form's error on every instance)
+    # and FP32 (what running them one by one in the same form would give)
+    def sequential(precision):
+        upd, secs, res = 0.0, 0.0, {}
+        per = 16 + (4 if precision == 32 else 8)
+        hs = {1: pp.Handle(64, precision=precision, max_terms=int(budget / 2.6 / per / 2)),
+              2: pp.Handle(128, precision=precision, max_terms=int(budget / 2.6 / (per + 16) / 2))}
         for r in reqs:
             h = hs[r.instance.W]
             h.load_instance(r.instance)
             t = time.perf_counter()
             try:
                 h.run_instance(r.instance)
-                e64 = h.pp_expect()
-                single_upd += h.pp_get_stats().updates
-                single_s += time.perf_counter() - t
-                o = by_rid[r.rid]
-                if o.status == pp.PP_OK:
-                    max_err = max(max_err, abs(o.expect - e64))
-                    n_cmp += 1
+                res[r.rid] = h.pp_expect()
+                upd += h.pp_get_stats().updates
             except pp.PPError:
-                single_s += time.perf_counter() - t
+                pass
+            secs += time.perf_counter() - t
         for h in hs.values():
             h.close()
+        return (upd / secs if secs > 0 else None), res
+
+    single64 = single32 = None
+    errs = []
+    if not args.no_single:
+        single64, e64 = sequential(64)
+        single32, _ = sequential(32)
+        for o in out:
+            if o.status == pp.PP_OK and o.rid in e64:
+                errs.append(abs(o.expect - e64[o.rid]))
     if rank != 0:
         return
     line = {"metric": METRIC, "value": summ["updates_per_s"], "unit": UNIT, "n_gpus": world,
@@ -389,8 +399,9 @@ def pool_arm(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f%d" % args.precision, "data": "synthetic",
             "config": cfg, "served": summ["served"], "failed": summ["failed"],
             "escalated": summ["escalated"], "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
-            "single_instance_fp64_updates_per_s": single_upd / single_s if single_s > 0 else None,
-            "fp32_vs_fp64_max_abs_err": max_err if n_cmp else None, "compared": n_cmp,
+            "single_instance_fp64_updates_per_s": single64, "single_instance_fp32_updates_per_s": single32,
+            "fp32_vs_fp64_abs_err": ({"max": max(errs), "median": statistics.median(errs)} if errs else None),
+            "compared": len(errs),
             "tuned": {k: list(tuner.best(k)) for k in sorted(tuner.samples)}}
     print(json.dumps(line), flush=True)
 
@@ -407,7 +418,7 @@ def main():
     ap.add_argument("--sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
-    ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--requests", type=int, default=150)
     ap.add_argument("--rate", type=float, default=4.0)
     ap.add_argument("--no-single", action="store_true")

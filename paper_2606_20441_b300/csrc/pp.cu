@@ -486,9 +486,15 @@ cudaError_t launch_smem_tier(pp_handle* h, const StepParams& p, int cap, uint32_
         if (e != cudaSuccess) return e;
         attr_set.store(smem);
     }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T, NT>, NT, smem);
-    per_sm = std::max(per_sm, 1);
+    // resident CTAs per SM: a property of the kernel and its shared memory,
+    // queried once (the query takes driver locks that concurrent handles share)
+    static std::atomic<int> occ(0);
+    int per_sm = occ.load();
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T, NT>, NT, smem);
+        per_sm = std::max(per_sm, 1);
+        occ.store(per_sm);
+    }
     uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(per_sm * h->sm_count));
     k_process<W, T, NT><<<grid, NT, smem, h->st>>>(p, cap);
     return cudaGetLastError();
@@ -508,9 +514,13 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t
                 if (e != cudaSuccess) return e;
                 attr_set.store(smem);
             }
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process_warp<W, T>, kTiers[0].threads, smem);
-            per_sm = std::max(per_sm, 1);
+            static std::atomic<int> occ(0);   // as in launch_smem_tier
+            int per_sm = occ.load();
+            if (per_sm == 0) {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process_warp<W, T>, kTiers[0].threads, smem);
+                per_sm = std::max(per_sm, 1);
+                occ.store(per_sm);
+            }
             uint32_t grid = std::min<uint32_t>(std::max<uint32_t>((n_items + WARP_TILE_WARPS - 1) / WARP_TILE_WARPS, 1),
                                                (uint32_t)(per_sm * h->sm_count));
             k_process_warp<W, T><<<grid, kTiers[0].threads, smem, h->st>>>(p, cap);

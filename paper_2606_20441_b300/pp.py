@@ -136,7 +136,8 @@ class Handle:
         if torch_memory:
             import torch
             dev = torch.cuda.current_device()
-            st = torch.cuda.current_stream() if stream is None else None
+            # blocks are cached per stream: allocate on the stream that uses them
+            st = torch.cuda.current_stream().cuda_stream if stream is None else stream
 
             def _alloc(nbytes, ctx):
                 return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
@@ -146,7 +147,7 @@ class Handle:
 
             self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
             opt.alloc, opt.free = self._cb
-            opt.cuda_stream = st.cuda_stream if st is not None else stream
+            opt.cuda_stream = st
         elif stream is not None:
             opt.cuda_stream = stream
         h = ctypes.c_void_p()

@@ -9,12 +9,14 @@ handles on its own CUDA stream, and the library's calls release the GIL.
 Admission by HBM budget.  The number of live strings a request will reach is
 not known before it runs, so the budget is divided up front into worker
 shares: `n_small` workers with equal small shares and `n_large` workers that
-split a large fraction of the budget.  Every worker owns one handle per mask
-width (W = 1 up to 64 qubits, W = 2 up to 128) whose term capacity is its
-share.  A request starts on whichever worker is free; if it outgrows a small
+split a large fraction of the budget.  A worker's handle (for the mask width of
+its request) has its share as term capacity.  A request starts on whichever worker is free; if it outgrows a small
 share (PP_ERR_CAPACITY) it is re-admitted, with its original arrival time, to
 the queue that only the large workers serve first.  A request that outgrows a
-large share is reported as failed.  Keeping the term arrays of a request on
+large share is reported as failed.  With a `route_key` (a workload-class
+function), a class that has needed a large share once sends its later requests
+straight to the large workers, so they do not first waste a small worker's
+time.  Keeping the term arrays of a request on
 the device between its layers is the library's ordinary behaviour.
 
 The executor is injectable so the scheduling logic can be exercised without a
@@ -55,8 +57,13 @@ class Outcome:
 
 class GpuExecutor:
     """Workers 0..n_small-1 hold small shares of the HBM budget, workers
-    n_small..n_small+n_large-1 hold large ones; each worker has its own CUDA
-    stream and one handle per mask width."""
+    n_small..n_small+n_large-1 hold large ones.  Each worker has its own CUDA
+    stream and one handle at a time, for the mask width of its current request
+    (W = 1 up to 64 qubits, W = 2 up to 128), with the whole share as its term
+    capacity.  Handles take their device memory from torch's caching
+    allocator, so replacing a worker's handle when the mask width changes
+    returns the memory to the cache instead of freeing it (a device free would
+    stall every stream on the GPU)."""
 
     def __init__(self, n_small: int, hbm_budget_bytes: float, precision: int = 32,
                  n_large: int = 0, large_fraction: float = 0.5, tuner=None):
@@ -67,27 +74,32 @@ class GpuExecutor:
         self.n_small = n_small
         self.n_large = n_large
         self.tuner = tuner
-        bytes_per = {1: 16 + (4 if precision == 32 else 8), 2: 32 + (4 if precision == 32 else 8)}
         frac_small = 1.0 - (large_fraction if n_large > 0 else 0.0)
-        shares = [hbm_budget_bytes * frac_small / n_small] * n_small
-        shares += [hbm_budget_bytes * large_fraction / n_large] * n_large
-        self.handles = []
-        self.streams = []
-        for share in shares:
-            st = torch.cuda.Stream()
-            self.streams.append(st)
-            hs = {}
-            # per handle: two term arenas, two overflow areas of a quarter arena
-            # and per-bucket counters, ~2.6 strings' worth per term of capacity;
-            # the share is split between the W = 1 and W = 2 handles
-            for W in (1, 2):
-                cap = int(share / 2.0 / (2.6 * bytes_per[W]))
-                hs[W] = pp.Handle(64 * W, precision=precision, max_terms=cap, stream=st.cuda_stream)
-            self.handles.append(hs)
+        self.shares = [hbm_budget_bytes * frac_small / n_small] * n_small
+        self.shares += [hbm_budget_bytes * large_fraction / n_large] * n_large
+        self.streams = [torch.cuda.Stream() for _ in self.shares]
+        self.current: List[Optional[tuple]] = [None] * len(self.shares)   # (W, Handle)
+
+    def capacity(self, worker: int, W: int) -> int:
+        # two term arenas, two overflow areas of a quarter arena and per-bucket
+        # counters: ~2.6 strings' worth of memory per term of capacity
+        per_string = 16 * W + (4 if self.precision == 32 else 8)
+        return int(self.shares[worker] / (2.6 * per_string))
+
+    def handle(self, worker: int, W: int):
+        cur = self.current[worker]
+        if cur is not None and cur[0] == W:
+            return cur[1]
+        if cur is not None:
+            cur[1].close()
+        h = self.pp.Handle(64 * W, precision=self.precision, max_terms=self.capacity(worker, W),
+                           torch_memory=True, stream=self.streams[worker].cuda_stream)
+        self.current[worker] = (W, h)
+        return h
 
     def run(self, worker: int, inst: "inputs.Instance"):
-        h = self.handles[worker][inputs.n_words(inst.n_qubits)]
         try:
+            h = self.handle(worker, inputs.n_words(inst.n_qubits))
             h.load_instance(inst)
             setting = self.tuner.apply(h, inst) if self.tuner is not None else None
             h.run_instance(inst)
@@ -100,9 +112,22 @@ class GpuExecutor:
             return ex.status, None, 0.0, 0
 
     def close(self):
-        for hs in self.handles:
-            for h in hs.values():
-                h.close()
+        for k, cur in enumerate(self.current):
+            if cur is not None:
+                cur[1].close()
+            self.current[k] = None
+
+
+def estimated_cost(inst: "inputs.Instance") -> float:
+    """A size proxy for ordering a batch: qubits times layers (the live-string
+    count grows with both)."""
+    return float(inst.n_qubits) * float(inst.n_layers)
+
+
+def batch_order(requests: List["inputs.Request"]) -> List["inputs.Request"]:
+    """Largest-first order for requests that are all present at once, so the
+    longest propagations start first and the short ones fill in around them."""
+    return sorted(requests, key=lambda r: (r.arrival_s, -estimated_cost(r.instance), r.rid))
 
 
 class Server:
@@ -111,11 +136,14 @@ class Server:
     re-admitted requests first, then ordinary ones."""
 
     def __init__(self, executor, n_workers: int, n_large: int = 0,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter,
+                 route_key: Optional[Callable] = None):
         self.executor = executor
         self.n_workers = n_workers
         self.n_large = n_large
         self.clock = clock
+        self.route_key = route_key
+        self.large_classes: set = set()
         self.outcomes: List[Outcome] = []
 
     def _worker(self, w: int, large: bool):
@@ -138,6 +166,8 @@ class Server:
             with self._cv:
                 if status == PP_ERR_CAPACITY and not large and self.n_large > 0:
                     self._escalated.append((req, arrival, True))
+                    if self.route_key is not None:
+                        self.large_classes.add(self.route_key(req.instance))
                 else:
                     self.outcomes.append(Outcome(req.rid, arrival, start, done, w, status, e, upd, terms,
                                                  escalated))
@@ -157,13 +187,17 @@ class Server:
         for t in workers:
             t.start()
         t0 = self.clock()
-        for req in sorted(requests, key=lambda r: r.arrival_s):
+        for req in sorted(requests, key=lambda r: r.arrival_s):   # stable: ties keep the given order
             due = t0 + req.arrival_s * time_scale
             wait = due - self.clock()
             if wait > 0:
                 time.sleep(wait)
             with self._cv:
-                self._fresh.append((req, max(due, t0), False))
+                if (self.n_large > 0 and self.route_key is not None
+                        and self.route_key(req.instance) in self.large_classes):
+                    self._escalated.append((req, max(due, t0), True))
+                else:
+                    self._fresh.append((req, max(due, t0), False))
                 self._cv.notify_all()
         with self._cv:
             self._closed = True

@@ -90,3 +90,28 @@ def test_large_worker_failures_are_final():
     assert all(o.worker == 2 for o in out)
     # each request ran at most once on a small worker, then once on the large one
     assert len(ex.order) <= 10
+
+
+def test_learned_routing_skips_small_workers():
+    """Once a class has needed a large share, its later requests go straight to
+    the large workers (each big request runs on a small worker at most once per
+    class, not once per request)."""
+    class Shares(FakeExecutor):
+        def run(self, worker, inst):
+            super().run(worker, inst)
+            if inst.n_qubits > 20 and worker < 2:
+                return serving.PP_ERR_CAPACITY, None, 0.0, 0
+            return 0, 1.0, 5.0, 1
+    reqs = inputs.workload_serving(count=24, rate_hz=100.0, side_hi=6, steps_hi=5)
+    big = [r for r in reqs if r.instance.n_qubits > 20]
+    assert len(big) >= 4
+    ex = Shares(0.003)
+    srv = serving.Server(ex, n_workers=2, n_large=1, route_key=lambda inst: inst.n_qubits > 20)
+    out = srv.serve(reqs)
+    assert all(o.status == 0 for o in out) and len(out) == 24
+    # every run of a big request beyond the first few was on the large worker:
+    # small-worker attempts are bounded by the requests in flight when the class
+    # was first learned (at most the two small workers' worth)
+    runs = len(ex.order)
+    assert runs - len(reqs) <= 2
+    assert srv.large_classes == {True}
