@@ -332,6 +332,8 @@ def pool_arm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build.build()
     eps, w_max = 1e-4, 8
+    if args.workers <= 0:
+        args.workers = 8 if args.workload == "batch64" else 12
     if args.workload == "batch64":
         insts = inputs.workload_batch64(eps=eps, w_max=w_max)
         reqs = serving.batch_order([inputs.Request(i, 0.0, inst) for i, inst in enumerate(insts)])
@@ -418,9 +420,9 @@ def main():
     ap.add_argument("--sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
-    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--workers", type=int, default=0, help="small-share workers (0: 8 for batch64, 12 for serve)")
     ap.add_argument("--requests", type=int, default=150)
-    ap.add_argument("--rate", type=float, default=4.0)
+    ap.add_argument("--rate", type=float, default=2.0)
     ap.add_argument("--no-single", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

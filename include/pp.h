@@ -123,9 +123,12 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
 pp_status pp_expect(pp_handle* h, double* value);
 
 /* Copies O~ to caller-owned host buffers, sorted by (x, then z) as unsigned
- * integers (word W-1 most significant).  x, z: [cap][W], c: [cap] (FP64 in both
- * precisions).  *n_out = number of terms; PP_ERR_CAPACITY if cap < *n_out (nothing
- * copied).  Any of x, z, c may be NULL to query *n_out only. */
+ * integers (word W-1 most significant).  The sort runs on the device (a radix
+ * sort of the result, which stays sorted in the handle); the host only copies.
+ * x, z: [cap][W], c: [cap] (FP64 in both precisions).  *n_out = number of
+ * terms; PP_ERR_CAPACITY if cap < *n_out or *n_out >= 2^32 (nothing copied);
+ * PP_ERR_NOMEM if the sort's scratch (~N/2 bytes, kept by the handle) cannot be
+ * allocated.  Any of x, z, c may be NULL to query *n_out only (no sort). */
 pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, double* c,
                           size_t* n_out);
 

@@ -16,6 +16,7 @@
 #include "pp.h"
 #include "pp_kernels.cuh"
 #include "pp_warp.cuh"
+#include "pp_result.cuh"
 
 using namespace pp;
 
@@ -111,7 +112,9 @@ struct pp_handle {
     int fb_cap = 0;                        // strings per global-tier tile
     uint64_t* stage = nullptr;     // input staging
     size_t stage_cap = 0;
-    __int128* partial = nullptr;
+    __int128* partial = nullptr;   // [4096] per-block partial sums, then the total
+    unsigned char* sort_scratch = nullptr;   // export sort: digit counts and scan sums
+    size_t sort_scratch_bytes = 0;
     std::vector<void*> owned;
 
     // result
@@ -464,7 +467,7 @@ pp_status ensure_memory(pp_handle* h) {
     for (int k = 0; k < N_TIERS - 1; ++k)
         if (!(h->pass_list[k] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap))))
             return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
-    h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * 4096));
+    h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * (4096 + 1)));
     if (!h->spill_b || !h->spill_s || !h->counters || !h->delta || !h->partial)
         return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     return PP_OK;
@@ -645,6 +648,62 @@ float eps_float_ceil(double eps) {
     float f = (float)eps;
     if ((double)f < eps) f = std::nextafter(f, INFINITY);
     return f;
+}
+
+}  // namespace
+
+namespace {
+
+// Orders the result's strings by key on the device (pp_result.cuh): radix
+// passes ping-pong between the two term arenas; the sorted result stays the
+// handle's result.
+template <int W, typename T>
+pp_status sort_result(pp_handle* h) {
+    const size_t N = h->n_res;
+    const uint32_t n_tiles = (uint32_t)((N + SORT_TILE - 1) / SORT_TILE);
+    const size_t L = (size_t)SORT_RADIX * n_tiles;
+    const size_t n_chunks = (L + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    const size_t bytes = 16 * 2 * W + 4 * (L + n_chunks);
+    if (bytes > h->sort_scratch_bytes) {
+        if (h->sort_scratch) {
+            CK(cudaStreamSynchronize(h->st));
+            dev_free(h, h->sort_scratch);
+        }
+        h->sort_scratch = static_cast<unsigned char*>(dev_alloc(h, bytes));
+        h->sort_scratch_bytes = h->sort_scratch ? bytes : 0;
+        if (!h->sort_scratch) return fail(h, PP_ERR_NOMEM, "export sort scratch allocation failed");
+    }
+    unsigned long long* varying = reinterpret_cast<unsigned long long*>(h->sort_scratch);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(h->sort_scratch + 16 * 2 * W);
+    uint32_t* sums = counts + L;
+    CK(cudaMemsetAsync(varying, 0, sizeof(unsigned long long) * 2 * W, h->st));
+    int cur = h->res_side;
+    {
+        const Arena& a = h->arena[cur];
+        const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)4 * h->sm_count);
+        k_sort_varying<W><<<grid, 256, 0, h->st>>>(a.x, a.z, h->cap, N, varying);
+        CK(cudaGetLastError());
+    }
+    unsigned long long vary[2 * W];
+    CK(cudaMemcpyAsync(vary, varying, sizeof(vary), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int kw = 0; kw < 2 * W; ++kw)
+        for (int shift = 0; shift < 64; shift += 8) {
+            if (((vary[kw] >> shift) & 0xffull) == 0) continue;   // one digit value in every key
+            const Arena& a = h->arena[cur];
+            const Arena& b = h->arena[cur ^ 1];
+            k_sort_hist<W><<<n_tiles, SORT_THREADS, 0, h->st>>>(a.x, a.z, h->cap, N, kw, shift, counts, n_tiles);
+            k_scan_chunks<<<(unsigned)n_chunks, SORT_THREADS, 0, h->st>>>(counts, L, sums);
+            k_scan_sums<<<1, SORT_THREADS, 0, h->st>>>(sums, (uint32_t)n_chunks);
+            k_scan_add<<<(unsigned)n_chunks, SORT_THREADS, 0, h->st>>>(counts, L, sums);
+            k_sort_scatter<W, T><<<n_tiles, SORT_THREADS, 0, h->st>>>(
+                a.x, a.z, static_cast<const T*>(a.c), h->cap, N, kw, shift, counts, n_tiles, b.x, b.z,
+                static_cast<T*>(b.c), h->cap);
+            CK(cudaGetLastError());
+            cur ^= 1;
+        }
+    h->res_side = cur;
+    return PP_OK;
 }
 
 }  // namespace
@@ -1115,11 +1174,12 @@ pp_status pp_expect(pp_handle* h, double* value) {
         else k_expect<2, double><<<grid, 256, 0, h->st>>>(a.x, (const double*)a.c, h->cap, h->n_res, h->partial);
     }
     CK(cudaGetLastError());
-    std::vector<__int128> part(grid);
-    CK(cudaMemcpyAsync(part.data(), h->partial, sizeof(__int128) * grid, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    k_expect_final<<<1, 256, 0, h->st>>>(h->partial, grid);
+    CK(cudaGetLastError());
     __int128 tot = 0;
-    for (auto v : part) tot += v;
+    CK(cudaMemcpyAsync(&tot, h->partial + grid, sizeof(__int128), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    // the exact fixed-point total (units of 2^-80), rounded once to double
     bool neg = tot < 0;
     unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
     long double v = (long double)(uint64_t)(mag >> 64) * 18446744073709551616.0L + (long double)(uint64_t)mag;
@@ -1137,6 +1197,13 @@ pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, do
     if (cap < h->n_res) return fail(h, PP_ERR_CAPACITY, "export buffer holds %zu < %zu terms", cap, h->n_res);
     const size_t N = h->n_res;
     const int W = h->W;
+    if (N >= (1ull << 32)) return fail(h, PP_ERR_CAPACITY, "export of %zu terms: at most 2^32 - 1", N);
+    if (N > 1) {
+        const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+        pp_status st = W == 1 ? (f32 ? sort_result<1, float>(h) : sort_result<1, double>(h))
+                              : (f32 ? sort_result<2, float>(h) : sort_result<2, double>(h));
+        if (st != PP_OK) return st;
+    }
     const Arena& a = h->arena[h->res_side];
     std::vector<uint64_t> hx(N * W), hz(N * W);
     std::vector<double> hc(N);
@@ -1153,22 +1220,13 @@ pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, do
         CK(cudaMemcpyAsync(hc.data(), a.c, N * 8, cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
     }
-    std::vector<size_t> idx(N);
-    for (size_t i = 0; i < N; ++i) idx[i] = i;
-    std::sort(idx.begin(), idx.end(), [&](size_t a_, size_t b_) {
-        for (int w = W - 1; w >= 0; --w)
-            if (hx[w * N + a_] != hx[w * N + b_]) return hx[w * N + a_] < hx[w * N + b_];
-        for (int w = W - 1; w >= 0; --w)
-            if (hz[w * N + a_] != hz[w * N + b_]) return hz[w * N + a_] < hz[w * N + b_];
-        return false;
-    });
+    // word-major device layout to the caller's [N][W] rows
     for (size_t k = 0; k < N; ++k) {
-        size_t i = idx[k];
         for (int w = 0; w < W; ++w) {
-            if (x) x[k * W + w] = hx[w * N + i];
-            if (z) z[k * W + w] = hz[w * N + i];
+            if (x) x[k * W + w] = hx[w * N + k];
+            if (z) z[k * W + w] = hz[w * N + k];
         }
-        if (c) c[k] = hc[i];
+        if (c) c[k] = hc[k];
     }
     return PP_OK;
 }
