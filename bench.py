@@ -132,16 +132,20 @@ def kernel_source_sha():
     return h.hexdigest()
 
 
-def profiled_traffic(strings_per_launch, precision):
+def profiled_traffic(strings_per_launch, precision, plan):
     """DRAM bytes per launch of the main-tier kernel from the committed ncu
-    summary, scaled by strings processed, or None when the kernel source
-    changed since the counters were taken."""
+    summary, scaled by strings processed, or None when the kernel source or
+    the plan (fused gates, bucket headroom: they set how full the buckets'
+    regions are) changed since the counters were taken."""
     if not os.path.exists(PROFILE):
         return None
     txt = open(PROFILE).read()
     m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
     m_tr = re.search(r"dram_bytes_per_string_fp%d:\s*([0-9.eE+]+)" % precision, txt)
-    if not m_sha or not m_tr or m_sha.group(1) != kernel_source_sha():
+    m_plan = re.search(r"plan:\s*max_fused_gates=(\d+)\s+bucket_headroom=([0-9.]+)", txt)
+    if not m_sha or not m_tr or not m_plan or m_sha.group(1) != kernel_source_sha():
+        return None
+    if (int(m_plan.group(1)), float(m_plan.group(2))) != (int(plan[0]), round(float(plan[1]), 6)):
         return None
     return float(m_tr.group(1)) * strings_per_launch
 
@@ -203,6 +207,7 @@ def ours_arm(args, rank, world, local_rank):
 
     inst = workload(args)
     h = pp.Handle(inst.n_qubits, precision=args.precision)
+    plan = h.pp_get_tuning()
     h.load_instance(inst)
     for _ in range(args.warmup):
         h.run_instance(inst)
@@ -293,8 +298,10 @@ def ours_arm(args, rank, world, local_rank):
                 "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": main_bytes, "avg_launch_ms": main_ms_avg,
-                "traffic": profiled_traffic(tier_strings[0] / max(1, tier_launches[0]), args.precision),
-                "share_of_step_time": (tier_ms[0] / 1000.0) / sec if sec > 0 else None}
+                "traffic": profiled_traffic(tier_strings[0] / max(1, tier_launches[0]), args.precision,
+                                            plan),
+                "share_of_step_time": (tier_ms[0] / 1000.0) / sec if sec > 0 else None,
+                "plan": {"max_fused_gates": plan[0], "bucket_headroom": plan[1]}}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         u, s_ = run_oracle_sample(args, args.sample_steps)

@@ -180,11 +180,11 @@ const char* pp_last_error(const pp_handle* h);
  * (Sec. I, Eq. evolve_gate, truncation after every gate); only the run time
  * does.
  *   max_fused_gates  commuting gates fused into one sub-layer (one pass over
- *                    the strings), 1..64*W; 0 = library default (16).  More
+ *                    the strings), 1..64*W; 0 = library default (32).  More
  *                    gates mean fewer passes but larger orbits per bucket.
  *   bucket_headroom  buckets are sized so that a bucket's strings times the
  *                    sub-layer's observed growth, times this factor, fill one
- *                    warp tile; in [1, 16]; 0 = library default (1.6).  Larger
+ *                    warp tile; in [1, 16]; 0 = library default (2.4).  Larger
  *                    values mean more, emptier buckets.
  * pp_set_tuning copies *t and takes effect at the next pp_propagate.
  * Errors: PP_ERR_ARG (NULL pointer, value out of range; the handle keeps its

@@ -24,7 +24,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 Setting = Tuple[int, float]   # (max_fused_gates, bucket_headroom)
 
-CANDIDATES: List[Setting] = [(16, 1.6), (8, 1.6), (32, 1.6), (16, 1.2), (16, 2.4), (24, 2.0)]
+CANDIDATES: List[Setting] = [(32, 2.4), (16, 1.6), (24, 2.0), (32, 1.6), (32, 3.2), (16, 2.4)]
 
 
 def class_key(inst) -> str:

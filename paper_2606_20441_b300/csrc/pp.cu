@@ -32,8 +32,8 @@ struct TierCfg {
 };
 constexpr TierCfg kTiers[N_TIERS] = {
     {32 * WARP_TILE_WARPS, 248, 248},   // one warp per bucket
-    {512, 1024, 1024},                  // CTA tiles
-    {1024, 4096, 2048},
+    {64, 1024, 1024},                   // CTA tiles: few warps, so that a round's
+    {256, 4096, 2048},                  // barriers wait on few warps
     {512, 1 << 20, 1 << 20}};           // global-memory tile
 constexpr int kGlobalTier = N_TIERS - 1;
 constexpr int kFallbackCTAs = 16; // CTAs of the global tier
@@ -224,14 +224,14 @@ int sig_kind(const SubLayerDesc& d) {
 // 2^(acting gates) strings, so smaller sub-layers keep orbits small enough for
 // the one-warp tiles at the price of more passes over the strings.
 int max_fused_gates(const pp_handle* h) {
-    // default: the measured best trade-off on the 6x6 and 7x8 TFIM workloads
-    int m = h->tune.max_fused_gates > 0 ? h->tune.max_fused_gates : 16;
+    // default: the measured best on the 7x8 TFIM workload (with bucket headroom 2.4)
+    int m = h->tune.max_fused_gates > 0 ? h->tune.max_fused_gates : 32;
     if (const char* e = getenv("PP_MAX_FUSED_GATES")) m = atoi(e);
     return std::max(1, std::min(m, 64 * h->W));
 }
 
 double bucket_headroom(const pp_handle* h) {
-    return h->tune.bucket_headroom > 0.0 ? h->tune.bucket_headroom : 1.6;
+    return h->tune.bucket_headroom > 0.0 ? h->tune.bucket_headroom : 2.4;
 }
 
 // Splits a layer's gates (listed order) into fused sub-layers.
