@@ -150,6 +150,18 @@ def profiled_traffic(strings_per_launch, precision, plan):
     return float(m_tr.group(1)) * strings_per_launch
 
 
+def replica_totals(sec, updates, device):
+    """Whole-job numbers of independent replicas (one per rank): the slowest
+    rank's time and the sum of all ranks' updates."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([sec], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([updates], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -246,12 +258,7 @@ def ours_arm(args, rank, world, local_rank):
     sec = e0.elapsed_time(e1) / 1000.0
     tot_updates = updates
     if dist:
-        t = torch.tensor([sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-        u = torch.tensor([updates], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u)
-        tot_updates = float(u.item())
+        sec, tot_updates = replica_totals(sec, updates, "cuda")
 
     # end-to-end through the C ABI with host buffers: load circuit and noise,
     # propagate the host observable, read the expectation back, every step

@@ -87,9 +87,10 @@ pp_status pp_destroy(pp_handle* h);
 /* Loads the circuit (Sec. I: time-ordered Pauli rotations U_t = exp(-i R_t theta_t / 2)).
  *   rx, rz     [n_gates][W] generator R of each gate
  *   theta      [n_gates]    rotation angle
- *   layer_of   [n_gates]    layer index, non-decreasing, >= 0; n_layers = last + 1
+ *   layer_of   [n_gates]    layer index of each gate, in [0, n_layers); any order:
+ *                           a layer's gates are applied in the order they are listed
  *                           (layers without gates are allowed and may carry noise)
- *   n_layers   number of layers (>= 1 + max(layer_of)); lets trailing layers be empty
+ *   n_layers   number of layers (>= 1); lets trailing layers be empty
  * Gates of one layer must pairwise commute (else PP_ERR_ARG).  Clears any
  * previously loaded noise.  cos/sin of each angle are taken on the host; values
  * with magnitude below 1e-15 snap to exactly 0 (and the other to +-1). */
