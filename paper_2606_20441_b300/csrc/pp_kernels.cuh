@@ -114,7 +114,7 @@ struct Tile {
     int* nact;        // [2] lengths of the two active lists
 };
 
-constexpr int NWARPS = 16;    // warps per CTA of every tier (512 threads)
+constexpr int NWARPS = 16;    // warps per CTA of the global-memory tier (512 threads)
 
 // Gates of the current sub-layer in listed order, staged in shared memory.
 template <int W, typename T>
