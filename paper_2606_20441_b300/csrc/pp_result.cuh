@@ -22,6 +22,8 @@ constexpr int SORT_ROUNDS = 8;                             // items per thread p
 constexpr int SORT_TILE = SORT_THREADS * SORT_ROUNDS;     // 2048 items per tile
 constexpr int SORT_RADIX = 256;
 constexpr int SCAN_CHUNK = SORT_THREADS * SORT_ROUNDS;    // elements per block of the scan
+static_assert(SORT_THREADS == SORT_RADIX, "one thread per digit value in the histogram and scatter kernels");
+static_assert(SORT_WARPS <= 32, "the warp offsets of a block scan fit one warp");
 
 // One block folds the per-block partials of k_expect into partial[n].
 __global__ void k_expect_final(__int128* partial, int n) {
