@@ -299,7 +299,8 @@ def workload_batch64(count: int = 64, eps: float = 1e-6, seed: int = SEED_BASE +
                      w_max: int = -1) -> List[Instance]:
     """64 independent instances: lattices 4x4..8x8, 5-25 steps, R_ZZ U[0.1,0.5),
     R_X U[0.2,0.9), random Z_i or Z_aZ_b, rates U[0,2e-3), eps = 1e-6 (the
-    benchmark uses eps = 1e-5 and w_max = 10: at 1e-6 most instances outgrow a GPU)."""
+    benchmark uses eps = 1e-4 and w_max = 8: at 1e-6, and at 1e-5 with w_max = 10,
+    most instances outgrow a GPU)."""
     rng = SplitMix64(seed)
     return [random_tfim(rng, "batch%02d" % i, 4, 8, 5, 25, eps, w_max=w_max) for i in range(count)]
 
