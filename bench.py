@@ -178,6 +178,66 @@ def run_oracle_sample(args, steps):
     return r.updates, time.perf_counter() - t
 
 
+def _oracle_updates(inst):
+    from oracle import oracle
+    return oracle.run(inst).updates
+
+
+def _oracle_warm(_):
+    from oracle import oracle
+    oracle.lib()
+    return 0
+
+
+def oracle_pool_baseline(instances, updates_hint, seconds=15.0, rate_guess=1.0e6):
+    """The oracle on the host's cores over a bounded sample of independent
+    instances: the smallest ones (by the GPU run's update counts) whose total,
+    at about `rate_guess` updates per second per core, fills about `seconds` of
+    every core; one spawned process per core.  Instances still running after
+    3 x `seconds` are abandoned and only the finished ones count."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    order = sorted(range(len(instances)), key=lambda k: updates_hint[k])
+    budget = rate_guess * seconds * cores
+    pick, tot = [], 0.0
+    for k in order:
+        u = updates_hint[k]
+        if u <= 0 or u > rate_guess * seconds or tot + u > budget:
+            continue
+        pick.append(k)
+        tot += u
+    if not pick:
+        return None
+    procs = min(cores, len(pick))
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(processes=procs)
+    try:
+        pool.map(_oracle_warm, range(procs), chunksize=1)   # start-up (import, load the oracle), untimed
+        t = time.perf_counter()
+        deadline = t + 3.0 * seconds
+        it = pool.imap_unordered(_oracle_updates, [instances[k] for k in pick], chunksize=1)
+        upd, done = 0.0, 0
+        while done < len(pick):
+            left = deadline - time.perf_counter()
+            if left <= 0:
+                break
+            try:
+                upd += it.next(timeout=left)
+                done += 1
+            except mp.TimeoutError:
+                break
+        sec = time.perf_counter() - t
+    finally:
+        pool.terminate()
+        pool.join()
+    if done == 0:
+        return None
+    return {"value": upd / sec, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": "%d of the %d instances (the smallest by update count; %d finished in the time "
+                      "bound), %.2g updates, one process per core, FP64 hash-map oracle, %.1f s"
+                      % (len(pick), len(instances), done, upd, sec)}
+
+
 # ----------------------------------------------------------------------------- arms
 
 def reference_arm(args, rank, world):
@@ -410,6 +470,11 @@ def pool_arm(args, rank, world, local_rank):
                 errs.append(abs(o.expect - e64[o.rid]))
     if rank != 0:
         return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        by_rid = {o.rid: o for o in out}
+        ok = [r for r in reqs if by_rid[r.rid].status == pp.PP_OK]
+        cpu = oracle_pool_baseline([r.instance for r in ok], [by_rid[r.rid].updates for r in ok])
     line = {"metric": METRIC, "value": summ["updates_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": summ["span_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f%d" % args.precision, "data": "synthetic",
@@ -417,7 +482,7 @@ def pool_arm(args, rank, world, local_rank):
             "escalated": summ["escalated"], "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
             "single_instance_fp64_updates_per_s": single64, "single_instance_fp32_updates_per_s": single32,
             "fp32_vs_fp64_abs_err": ({"max": max(errs), "median": statistics.median(errs)} if errs else None),
-            "compared": len(errs),
+            "compared": len(errs), "cpu_baseline": cpu,
             "tuned": {k: list(tuner.best(k)) for k in sorted(tuner.samples)}}
     print(json.dumps(line), flush=True)
 
