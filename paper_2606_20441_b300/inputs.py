@@ -352,6 +352,146 @@ def mirror_instance(inst: Instance) -> Instance:
                                n_layers=2 * L, noise=[])
 
 
+# --------------------------------------------------------------------------- paper-shaped variants
+
+def heavy_hex_56() -> Tuple[int, List[Tuple[int, int]], List[int]]:
+    """A 56-qubit heavy-hex patch (the connectivity of the Sec. III device
+    runs): three rows of 16 qubits, joined by 4 bridge qubits between rows 0
+    and 1 (at columns 0, 4, 8, 12) and 4 between rows 1 and 2 (at columns 2, 6,
+    10, 14).  Indices: row 0 = 0..15, bridges 16..19, row 1 = 20..35, bridges
+    36..39, row 2 = 40..55.  Returns (n, edges, colour) with a proper 3-edge
+    colouring (each colour a matching: one layer of two-qubit gates): rows 0
+    and 2 alternate colours 0, 1 along the row, row 1 repeats 2, 0, 2, 1; the
+    upper bridges take colours 2 (to row 0) and 0 (to row 1), the lower ones 1
+    (to row 1) and 2 (to row 2), which are the colours free at their ends."""
+    base = [0, 20, 40]
+    row_pattern = [[0, 1, 0, 1], [2, 0, 2, 1], [0, 1, 0, 1]]
+    edges, colour = [], []
+    for r in range(3):
+        for c in range(15):
+            edges.append((base[r] + c, base[r] + c + 1))
+            colour.append(row_pattern[r][c % 4])
+    for k, c in enumerate((0, 4, 8, 12)):
+        b = 16 + k
+        edges += [(base[0] + c, b), (b, base[1] + c)]
+        colour += [2, 0]
+    for k, c in enumerate((2, 6, 10, 14)):
+        b = 36 + k
+        edges += [(base[1] + c, b), (b, base[2] + c)]
+        colour += [1, 2]
+    return 56, edges, colour
+
+
+def layered_instance(name: str, n: int, layers: Sequence[Sequence[Tuple[dict, float]]],
+                     noise_layers: Sequence[int], gens: Tuple[np.ndarray, np.ndarray],
+                     rates: np.ndarray, obs: Sequence[Tuple[dict, float]], eps: float = 0.0,
+                     w_max: int = -1, noise_mode: int = NOISE_INVERSE,
+                     meta: Optional[dict] = None) -> Instance:
+    """A circuit given as layers (time order) of commuting rotations, each a
+    (Pauli letters, angle) pair; noise with generators `gens` and the rates of
+    row k of `rates` follows layer noise_layers[k]."""
+    W = n_words(n)
+    gx, gz, th, lay = [], [], [], []
+    for l, gates in enumerate(layers):
+        for letters, theta in gates:
+            x, z = pauli_from_letters(letters, W)
+            gx.append(x); gz.append(z); th.append(float(theta)); lay.append(l)
+    ex, ez = gens
+    noise = [NoiseLayer(int(l), ex.copy(), ez.copy(), np.asarray(rates[k], dtype=np.float64).copy(), noise_mode)
+             for k, l in enumerate(noise_layers)]
+    ox, oz, oc = [], [], []
+    for letters, c in obs:
+        x, z = pauli_from_letters(letters, W)
+        ox.append(x); oz.append(z); oc.append(float(c))
+    return Instance(name=name, n_qubits=n,
+                    gate_x=np.array(gx, dtype=np.uint64).reshape(-1, W),
+                    gate_z=np.array(gz, dtype=np.uint64).reshape(-1, W),
+                    theta=np.array(th, dtype=np.float64),
+                    layer_of=np.array(lay, dtype=np.int32), n_layers=len(layers),
+                    noise=noise,
+                    obs_x=np.array(ox, dtype=np.uint64).reshape(-1, W),
+                    obs_z=np.array(oz, dtype=np.uint64).reshape(-1, W),
+                    obs_c=np.array(oc, dtype=np.float64),
+                    eps=float(eps), w_max=int(w_max), meta=dict(meta or {}))
+
+
+def _mirror_layers(forward: List[List[Tuple[dict, float]]]) -> List[List[Tuple[dict, float]]]:
+    """The forward layers, then their inverses in reverse order (angles negated)."""
+    back = [[(letters, -theta) for (letters, theta) in reversed(gates)] for gates in reversed(forward)]
+    return forward + back
+
+
+def workload_heavy_hex_mirror(steps: int = 4, theta: float = 0.3, rate_hi: float = 1e-3,
+                              obs_edge: Tuple[int, int] = (21, 22), eps: float = 1e-5, w_max: int = 10,
+                              seed: int = SEED_BASE + 6, noise_mode: int = NOISE_INVERSE) -> Instance:
+    """Sec. III shape: a mirror circuit of first-order TFIM Trotter steps on the
+    56-qubit heavy-hex patch.  Forward step: R_X(theta) on every site, then one
+    R_ZZ(theta) layer per edge colour (3 layers); the backward half inverts
+    the forward half.  Every R_ZZ layer (both halves) is followed by its own
+    noise map: X, Y, Z on every site and the 9 letter pairs on every edge,
+    rates uniform [0, rate_hi), drawn layer by layer.  With `steps` = 4 there
+    are 24 R_ZZ layers (48 CZ layers once each R_ZZ is compiled to two).  The
+    observable is Z_a Z_b on one edge (a weight-2 ZZ, as in the device runs)."""
+    n, edges, colour = heavy_hex_56()
+    fwd: List[List[Tuple[dict, float]]] = []
+    for _ in range(steps):
+        fwd.append([({q: "X"}, theta) for q in range(n)])
+        for col in range(3):
+            fwd.append([({a: "Z", b: "Z"}, theta) for (a, b), cc in zip(edges, colour) if cc == col])
+    layers = _mirror_layers(fwd)
+    zz = [l for l, gates in enumerate(layers) if len(next(iter(gates))[0]) == 2]
+    gens = lattice_generators(n, edges, n_words(n))
+    rng = SplitMix64(seed)
+    rates = draw_rates(rng, len(zz), gens[0].shape[0], rate_hi)
+    return layered_instance("heavyhex56_mirror_s%d" % steps, n, layers, zz, gens, rates,
+                            [({obs_edge[0]: "Z", obs_edge[1]: "Z"}, 1.0)], eps=eps, w_max=w_max,
+                            noise_mode=noise_mode, meta=dict(steps=steps, theta=theta, edges=edges,
+                                                             colour=colour))
+
+
+def workload_trotter2_mirror_3x3(steps: int = 2, theta: float = 0.05, rate_hi: float = 1e-3,
+                                 seed: int = SEED_BASE + 7, eps: float = 0.0,
+                                 noise_mode: int = NOISE_INVERSE) -> Instance:
+    """Sec. II / Fig. 2a shape: the 3x3 lattice evolved forwards, then
+    backwards, under second-order Trotter steps of the TFIM: R_X(theta/2),
+    then the R_ZZ(theta) edge colours one layer each, then R_X(theta/2).  Each
+    two-qubit layer is followed by the noise model of its colour: four models,
+    one per colour, drawn once and reused; generators X on every site and ZZ on
+    every edge (the paper's {X, ZZ} set), rates uniform [0, rate_hi).  The
+    observable is Z on all nine qubits."""
+    rows = cols = 3
+    n = rows * cols
+    edges, colour = square_lattice(rows, cols)
+    half = [({q: "X"}, 0.5 * theta) for q in range(n)]
+    fwd: List[List[Tuple[dict, float]]] = []
+    for _ in range(steps):
+        fwd.append(list(half))
+        for col in range(4):
+            fwd.append([({a: "Z", b: "Z"}, theta) for (a, b), cc in zip(edges, colour) if cc == col])
+        fwd.append(list(half))
+    layers = _mirror_layers(fwd)
+    W = n_words(n)
+    ex, ez = [], []
+    for q in range(n):
+        x, z = pauli_from_letters({q: "X"}, W); ex.append(x); ez.append(z)
+    for (a, b) in edges:
+        x, z = pauli_from_letters({a: "Z", b: "Z"}, W); ex.append(x); ez.append(z)
+    gens = (np.array(ex, dtype=np.uint64).reshape(-1, W), np.array(ez, dtype=np.uint64).reshape(-1, W))
+    rng = SplitMix64(seed)
+    models = draw_rates(rng, 4, gens[0].shape[0], rate_hi)
+    zz_layers, zz_models = [], []
+    for l, gates in enumerate(layers):
+        letters = gates[0][0]
+        if len(letters) == 2:
+            a, b = sorted(letters)
+            zz_layers.append(l)
+            zz_models.append(colour[edges.index((a, b))])
+    rates = models[np.array(zz_models, dtype=np.int64)]
+    return layered_instance("trotter2_mirror_3x3_s%d" % steps, n, layers, zz_layers, gens, rates,
+                            [({q: "Z" for q in range(n)}, 1.0)], eps=eps, noise_mode=noise_mode,
+                            meta=dict(steps=steps, theta=theta))
+
+
 def random_pauli_letters(rng: SplitMix64, sites: Sequence[int]) -> dict:
     return {q: "XYZ"[rng.randint(3)] for q in sites}
 
