@@ -178,6 +178,20 @@ def run_oracle_sample(args, steps):
     return r.updates, time.perf_counter() - t
 
 
+def host_cpu():
+    """The host's CPU model and logical core count, for the baseline lines."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def _oracle_updates(inst):
     from oracle import oracle
     return oracle.run(inst).updates
@@ -232,7 +246,7 @@ def oracle_pool_baseline(instances, updates_hint, seconds=15.0, rate_guess=1.0e6
         pool.join()
     if done == 0:
         return None
-    return {"value": upd / sec, "unit": UNIT, "cores": procs, "kind": "oracle",
+    return {"value": upd / sec, "unit": UNIT, "cores": procs, "kind": "oracle", "host": host_cpu(),
             "sample": "%d of the %d instances (the smallest by update count; %d finished in the time "
                       "bound), %.2g updates, one process per core, FP64 hash-map oracle, %.1f s"
                       % (len(pick), len(instances), done, upd, sec)}
@@ -259,7 +273,8 @@ def reference_arm(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, inst), "impl": "reference",
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -372,7 +387,7 @@ def ours_arm(args, rank, world, local_rank):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         u, s_ = run_oracle_sample(args, args.sample_steps)
-        cpu = {"value": u / s_, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": u / s_, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": "%s cut to its first %d Trotter steps (%.3g updates in %.1f s), "
                          "single-threaded FP64 hash-map oracle" % (args.workload, args.sample_steps, u, s_)}
     line = {"metric": METRIC, "value": tot_updates / sec, "unit": UNIT, "n_gpus": world,
