@@ -181,12 +181,17 @@ def heisenberg_coefficients(inst) -> np.ndarray:
     return pauli_coefficients(heisenberg_matrix(inst), inst.n_qubits)
 
 
-def ptm_propagate(inst, zero_tol: float = 1e-13) -> Dict[Tuple[int, int], float]:
+def ptm_propagate(inst, zero_tol: float = 1e-13, count_updates: bool = False):
     """Brute force over all 4^n Paulis (n <= 4) with truncation after every gate
     and every noise map.  Returns {(x, z): c} for the surviving strings.
 
     Dense traces leave rounding residue (~1e-17) on coefficients that are zero
-    exactly; entries below `zero_tol` in magnitude count as exact zeros."""
+    exactly; entries below `zero_tol` in magnitude count as exact zeros.
+
+    With count_updates, also returns the canonical gate-by-gate work count:
+    the number of surviving strings entering each gate, summed over gates
+    (counted here on the dense coefficient vector, independently of any hash
+    map), as (coef, updates)."""
     n = inst.n_qubits
     assert n <= 5
     dim = 1 << n
@@ -220,6 +225,7 @@ def ptm_propagate(inst, zero_tol: float = 1e-13) -> Dict[Tuple[int, int], float]
         k = (_int_mask(inst.obs_x[t], n), _int_mask(inst.obs_z[t], n))
         coef[k] = coef.get(k, 0.0) + float(inst.obs_c[t])
     coef = truncate(coef)
+    updates = 0
     noise_at: Dict[int, list] = {}
     for m in inst.noise:
         noise_at.setdefault(m.layer, []).append(m)
@@ -227,6 +233,7 @@ def ptm_propagate(inst, zero_tol: float = 1e-13) -> Dict[Tuple[int, int], float]
         for m in noise_at.get(l, []):
             coef = truncate(decompose(_apply_noise(compose(coef), m, n)))
         for g in np.nonzero(inst.layer_of == l)[0]:
+            updates += sum(1 for c in coef.values() if c != 0.0)
             U = _gate_unitary(inst, g, n)
             coef = truncate(decompose(U.conj().T @ compose(coef) @ U))
-    return coef
+    return (coef, updates) if count_updates else coef

@@ -117,8 +117,11 @@ def test_theta_zero_line_diagram(rows, cols, steps, after):
     edges, _ = inputs.square_lattice(rows, cols)
     obs = [({0: "Z"}, 0.5), ({1: "X", 2: "Y"}, -0.25), ({edges[-1][0]: "Y", edges[-1][1]: "Z"}, 1.0)]
     inst = inputs.tfim_instance("zero", rows, cols, steps, 0.0, 0.0, rates, obs, noise_after=after)
-    res = as_dict(oracle.run(inst), n)
+    run = oracle.run(inst)
+    res = as_dict(run, n)
     assert len(res) == len(obs)
+    # nothing branches at theta = 0, so every gate sees exactly the |O| strings
+    assert run.updates == inst.n_gates * len(obs)
     for t in range(len(obs)):
         s_tot = 0.0
         for m in inst.noise:
@@ -146,8 +149,11 @@ def test_clifford_points_single_path(rows, cols, steps):
     inst = inputs.tfim_instance("cliff", rows, cols, steps, math.pi / 2, tx, rates, obs)
     ref = clifford.propagate(inst)
     ref = {k: v for k, v in ref.items() if v != 0.0}
-    got = as_dict(oracle.run(inst), n)
+    run = oracle.run(inst)
+    got = as_dict(run, n)
     assert set(got) == set(ref)
+    # one path per string: every gate sees exactly the |O| strings
+    assert run.updates == inst.n_gates * len(obs)
     for k, v in ref.items():
         assert abs(got[k] - v) <= 1e-13 * abs(v)
 
@@ -185,14 +191,49 @@ def test_bruteforce_all_paulis_with_truncation(seed):
     eps = [0.0, 1e-3, 3e-2, 0.1][seed % 4]
     w_max = [-1, -1, 2, 1][(seed // 2) % 4]
     inst = inputs.random_circuit(seed, n, n_layers=6, eps=eps, w_max=w_max, rate_hi=0.1)
-    ref = dense.ptm_propagate(inst)
-    got = as_dict(oracle.run(inst), n)
+    ref, ref_updates = dense.ptm_propagate(inst, count_updates=True)
+    run = oracle.run(inst)
+    got = as_dict(run, n)
     margin = 1e-9
     near = {k for k, v in list(ref.items()) + list(got.items())
             if eps > 0 and abs(abs(v) - eps) <= margin * eps}
     assert set(got) - near == set(ref) - near
     for k in set(got) & set(ref):
         assert abs(got[k] - ref[k]) <= 1e-12
+    # the canonical work count (live strings entering each gate), counted on
+    # the dense coefficient vector
+    if not near:
+        assert run.updates == ref_updates
+
+
+@pytest.mark.parametrize("n,eps", [(6, 0.0), (9, 0.0), (8, 0.05), (10, 0.02)])
+def test_update_count_closed_form(n, eps):
+    """O = Z on n qubits, one layer of R_X(theta_j) on every site: gate j sees
+    every product of the cos/sin factors of gates 0..j-1 whose magnitude is at
+    least eps (each product is one string; truncation after every gate).  With
+    eps = 0 that is 2^j strings, a total of 2^n - 1."""
+    rng = inputs.SplitMix64(40 + n)
+    theta = [rng.uniform(0.3, 1.2) * (1 if rng.uniform() < 0.5 else -1) for _ in range(n)]
+    gx = np.zeros((n, 1), np.uint64)
+    gz = np.zeros((n, 1), np.uint64)
+    for q in range(n):
+        gx[q, 0] = np.uint64(1) << np.uint64(q)
+    ox, oz = inputs.pauli_from_letters({q: "Z" for q in range(n)}, 1)
+    inst = inputs.Instance("cf", n, gx, gz, np.array(theta), np.zeros(n, np.int32), 1, [],
+                           ox.reshape(1, 1), oz.reshape(1, 1), np.array([1.0]), eps=eps)
+    expected = 0
+    for j in range(n):
+        # products of a cos-or-sin factor per gate 0..j-1, each kept at every
+        # prefix (truncation after every gate drops a branch for good)
+        live = [1.0]
+        for t in range(j):
+            live = [v * f for v in live for f in (math.cos(theta[t]), math.sin(theta[t]))
+                    if abs(v * f) >= eps]
+        expected += len(live)
+    if eps == 0.0:
+        assert expected == 2 ** n - 1
+    run = oracle.run(inst)
+    assert run.updates == expected
 
 
 def test_dense_density_matches_small_random():
