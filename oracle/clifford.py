@@ -61,8 +61,23 @@ def clifford_trig(theta: float) -> Tuple[int, int]:
     return [(1, 0), (0, 1), (-1, 0), (0, -1)][kr % 4]
 
 
-def propagate(inst) -> Dict[Tuple[int, int], float]:
-    """{(x int, z int): c} for an instance whose angles are all Clifford."""
+def propagate(inst, truncate: bool = False, count_updates: bool = False):
+    """{(x int, z int): c} for an instance whose angles are all Clifford.
+
+    With truncate, a path ends as soon as its string would be dropped after a
+    gate or a noise map (Sec. I.A: |c| < eps or weight > w_max, checked after
+    every gate and every noise map; the input observable is checked first).
+    With count_updates, also returns the number of live strings entering each
+    gate summed over gates (one per path per gate it is alive at), as
+    (out, updates)."""
+    eps = float(inst.eps) if truncate else 0.0
+    w_max = int(inst.w_max) if truncate else -1
+
+    def dropped(px, pz, c):
+        if not truncate:
+            return False
+        return c == 0.0 or abs(c) < eps or (w_max >= 0 and bin(px | pz).count("1") > w_max)
+    updates = 0
     n = inst.n_qubits
     gates = [(_to_int(inst.gate_x[g]), _to_int(inst.gate_z[g]), clifford_trig(float(inst.theta[g])),
               int(inst.layer_of[g])) for g in range(inst.n_gates)]
@@ -74,22 +89,33 @@ def propagate(inst) -> Dict[Tuple[int, int], float]:
     for t in range(len(inst.obs_c)):
         px, pz = _to_int(inst.obs_x[t]), _to_int(inst.obs_z[t])
         c = float(inst.obs_c[t])
+        alive = not dropped(px, pz, c)
         for l in range(inst.n_layers - 1, -1, -1):
+            if not alive:
+                break
             for gens, mode in noise_at.get(l, []):
                 s = sum(lam for (ex, ez, lam) in gens if symplectic(px, pz, ex, ez))
                 c *= math.exp(2.0 * s) if mode == 0 else math.exp(-2.0 * s)
+                if dropped(px, pz, c):
+                    alive = False
             for (rx, rz, (cs, sn), lay) in gates:
-                if lay != l or not symplectic(px, pz, rx, rz):
+                if not alive or lay != l:
+                    continue
+                updates += 1
+                if not symplectic(px, pz, rx, rz):
                     continue
                 if sn == 0:
                     c *= cs
-                    continue
-                # U^dag P U = cos P + i sin R P, and i R P = i^{1+e} (R xor P)
-                e = product_phase(rx, rz, px, pz, n)
-                tot = (1 + e) % 4
-                assert tot in (0, 2)
-                c *= sn * (1 if tot == 0 else -1)
-                px, pz = px ^ rx, pz ^ rz
-        key = (px, pz)
-        out[key] = out.get(key, 0.0) + c
-    return out
+                else:
+                    # U^dag P U = cos P + i sin R P, and i R P = i^{1+e} (R xor P)
+                    e = product_phase(rx, rz, px, pz, n)
+                    tot = (1 + e) % 4
+                    assert tot in (0, 2)
+                    c *= sn * (1 if tot == 0 else -1)
+                    px, pz = px ^ rx, pz ^ rz
+                if dropped(px, pz, c):
+                    alive = False
+        if alive:
+            key = (px, pz)
+            out[key] = out.get(key, 0.0) + c
+    return (out, updates) if count_updates else out

@@ -54,6 +54,7 @@ class _Problem(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("w_max", ctypes.c_int),
         ("record", ctypes.c_int),
+        ("top_k", ctypes.c_int64),
     ]
 
 
@@ -92,7 +93,7 @@ def _ptr(a: np.ndarray):
 
 
 def run(inst, record: bool = False, eps: Optional[float] = None,
-        w_max: Optional[int] = None) -> OracleResult:
+        w_max: Optional[int] = None, top_k: Optional[int] = None) -> OracleResult:
     L = lib()
     W = inst.W
     keep = []
@@ -128,7 +129,8 @@ def run(inst, record: bool = False, eps: Optional[float] = None,
                   _ptr(noff).value, _ptr(ex).value, _ptr(ez).value, _ptr(lam).value,
                   _ptr(nm).value, len(oc), _ptr(ox).value, _ptr(oz).value,
                   _ptr(oc).value, float(inst.eps if eps is None else eps),
-                  int(inst.w_max if w_max is None else w_max), int(record))
+                  int(inst.w_max if w_max is None else w_max), int(record),
+                  int(getattr(inst, "top_k", 0) if top_k is None else top_k))
     h = L.orc_run(ctypes.byref(pb))
     try:
         err = L.orc_error(h)

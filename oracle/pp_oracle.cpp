@@ -179,6 +179,7 @@ typedef struct {
     double eps;
     int w_max;                  // < 0: no cap
     int record;                 // record per-gate mass bookkeeping
+    int64_t top_k;              // > 0: keep at most this many terms after each layer
 } orc_problem;
 
 typedef struct {
@@ -197,6 +198,23 @@ static bool keep(double c, const Key& k, double eps, int w_max, int W) {
     if (std::fabs(c) < eps) return false;
     if (w_max >= 0 && weight(k, W) > w_max) return false;
     return true;
+}
+
+// Top-K truncation (Sec. I.A: keep at most the K largest Pauli terms of an
+// intermediate result), applied to the input observable and after the gates
+// of every layer.  Terms are ranked by |c| descending; equal magnitudes are
+// ranked by the string, in the export order (x words from the most
+// significant, then z words), smallest first; the first K are kept.
+static void keep_top_k(Sum& cur, int64_t k) {
+    if (k <= 0 || (int64_t)cur.size() <= k) return;
+    std::vector<std::pair<Key, double>> all(cur.begin(), cur.end());
+    std::sort(all.begin(), all.end(), [](const std::pair<Key, double>& a, const std::pair<Key, double>& b) {
+        const double ma = std::fabs(a.second), mb = std::fabs(b.second);
+        if (ma != mb) return ma > mb;
+        return key_less(a.first, b.first);
+    });
+    cur.clear();
+    for (int64_t i = 0; i < k; ++i) cur.insert(all[(size_t)i]);
 }
 
 static void trig(double theta, double* c, double* s) {
@@ -226,6 +244,7 @@ orc_result* orc_run(const orc_problem* pb) {
         if (!keep(it->second, it->first, pb->eps, pb->w_max, W)) it = cur.erase(it);
         else ++it;
     }
+    keep_top_k(cur, pb->top_k);
     double updates = 0.0;
     int64_t peak = (int64_t)cur.size();
 
@@ -292,6 +311,7 @@ orc_result* orc_run(const orc_problem* pb) {
                 res->records->push_back(m_drop);
             }
         }
+        keep_top_k(cur, pb->top_k);
     }
 
     std::vector<std::pair<Key, double>> out(cur.begin(), cur.end());

@@ -109,6 +109,7 @@ class Instance:
     eps: float = 0.0
     w_max: int = -1
     meta: dict = dataclasses.field(default_factory=dict)
+    top_k: int = 0           # > 0: keep at most this many terms after each layer
 
     @property
     def W(self) -> int:

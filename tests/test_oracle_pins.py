@@ -158,6 +158,26 @@ def test_clifford_points_single_path(rows, cols, steps):
         assert abs(got[k] - v) <= 1e-13 * abs(v)
 
 
+def test_clifford_paths_with_truncation():
+    """The 7x8 benchmark circuit at Clifford angles with its threshold and
+    weight cap: single paths that end when the weight exceeds the cap (Sec.
+    I.A, truncation after every gate), followed by the symplectic tableau,
+    against the oracle's hash map: same strings, coefficients, update count."""
+    base = inputs.workload_7x8(eps=1e-6, w_max=10, steps=20)
+    rng = inputs.SplitMix64(3)
+    tx = [[0.0, math.pi / 2, math.pi, -math.pi / 2][rng.randint(4)] for _ in range(56)]
+    inst = inputs.tfim_instance("cliff78", 7, 8, 20, math.pi / 2, tx, np.stack([m.lam for m in base.noise]),
+                                [({a: "Z", b: "Z"}, 1.0 / 97) for (a, b) in base.meta["edges"]],
+                                eps=1e-6, w_max=10)
+    ref, ref_updates = clifford.propagate(inst, truncate=True, count_updates=True)
+    run = oracle.run(inst)
+    got = as_dict(run, 56)
+    assert 0 < len(ref) < len(inst.obs_c) and set(got) == set(ref)
+    for k, v in ref.items():
+        assert abs(got[k] - v) <= 1e-13 * abs(v)
+    assert run.updates == ref_updates
+
+
 # ----------------------------------------------------------------- dense simulation
 
 @pytest.mark.slow
@@ -295,3 +315,92 @@ def test_rotation_mass_bookkeeping():
     assert np.all(np.abs(rec[:, 1] - rec[:, 0]) <= 1e-12 * rec[:, 0])
     assert np.all(np.abs(rec[:, 2] + rec[:, 3] - rec[:, 1]) <= 1e-12 * rec[:, 1])
     assert np.sum(rec[:, 3]) > 0.0    # the threshold did act
+
+
+# ----------------------------------------------------------------- top-K truncation
+
+def _export_order_key(x_words, z_words):
+    """Sort key of a string in export order: x words from the most significant,
+    then z words."""
+    return tuple(int(v) for v in x_words[::-1]) + tuple(int(v) for v in z_words[::-1])
+
+
+def _obs_only(n, terms):
+    """An instance with one empty layer: the observable itself."""
+    W = inputs.n_words(n)
+    ox, oz, oc = [], [], []
+    for letters, c in terms:
+        x, z = inputs.pauli_from_letters(letters, W)
+        ox.append(x); oz.append(z); oc.append(c)
+    return inputs.Instance("obs", n, np.zeros((0, W), np.uint64), np.zeros((0, W), np.uint64), np.zeros(0),
+                           np.zeros(0, np.int32), 1, [], np.array(ox).reshape(-1, W),
+                           np.array(oz).reshape(-1, W), np.array(oc))
+
+
+def test_top_k_keeps_largest_magnitudes():
+    """Sec. I.A keeps the K largest terms: on a sum with distinct magnitudes,
+    exactly the K of largest |c| survive, with their coefficients."""
+    rng = inputs.SplitMix64(77)
+    terms = []
+    seen = set()
+    while len(terms) < 60:
+        sites = sorted({rng.randint(70) for _ in range(1 + rng.randint(4))})
+        letters = inputs.random_pauli_letters(rng, sites)
+        key = tuple(sorted(letters.items()))
+        if key in seen:
+            continue
+        seen.add(key)
+        terms.append((letters, rng.uniform(-1, 1)))
+    inst = _obs_only(70, terms)
+    for k in (1, 10, 59):
+        r = oracle.run(inst, top_k=k)
+        want = sorted(np.abs(inst.obs_c), reverse=True)[:k]
+        assert len(r.c) == k
+        assert sorted(np.abs(r.c), reverse=True) == want
+    # K >= N keeps everything
+    assert len(oracle.run(inst, top_k=60).c) == 60 and len(oracle.run(inst, top_k=10**6).c) == 60
+
+
+def test_top_k_ties_break_by_string_order():
+    """Equal magnitudes: the strings that come first in export order are kept."""
+    rng = inputs.SplitMix64(5)
+    terms, seen = [], set()
+    while len(terms) < 20:
+        q = rng.randint(9)
+        letters = {q: "XYZ"[rng.randint(3)], (q + 1 + rng.randint(8)) % 9: "XYZ"[rng.randint(3)]}
+        key = tuple(sorted(letters.items()))
+        if key in seen:
+            continue
+        seen.add(key)
+        terms.append((letters, 0.5 if rng.uniform() < 0.5 else -0.5))
+    inst = _obs_only(9, terms)
+    r = oracle.run(inst, top_k=7)
+    order = sorted(range(20), key=lambda t: _export_order_key(inst.obs_x[t], inst.obs_z[t]))[:7]
+    want = {_export_order_key(inst.obs_x[t], inst.obs_z[t]) for t in order}
+    got = {_export_order_key(r.x[i], r.z[i]) for i in range(len(r.c))}
+    assert got == want
+
+
+def test_top_k_after_a_layer_closed_form():
+    """One R_X layer on Z^n (eps = 0): the layer produces every product of a
+    cos-or-sin factor per site (the sin sites carry Y); top-K after the layer
+    keeps the K products of largest magnitude (ties by string order)."""
+    n, k = 9, 37
+    rng = inputs.SplitMix64(123)
+    theta = [rng.uniform(0.3, 1.2) for _ in range(n)]
+    gx = np.array([[1 << q] for q in range(n)], dtype=np.uint64)
+    gz = np.zeros((n, 1), np.uint64)
+    ox, oz = inputs.pauli_from_letters({q: "Z" for q in range(n)}, 1)
+    inst = inputs.Instance("tk", n, gx, gz, np.array(theta), np.zeros(n, np.int32), 1, [], ox.reshape(1, 1),
+                           oz.reshape(1, 1), np.array([1.0]))
+    prods = []
+    for m in range(1 << n):
+        v = 1.0
+        for q in range(n):
+            v = v * (math.sin(theta[q]) if (m >> q) & 1 else math.cos(theta[q]))
+        prods.append((-abs(v), m))
+    prods.sort()
+    want = {m for _, m in prods[:k]}
+    r = oracle.run(inst, top_k=k)
+    assert {int(r.x[i, 0]) for i in range(len(r.c))} == want
+    assert np.all(r.z[:, 0] == (1 << n) - 1)
