@@ -41,9 +41,9 @@ from paper_2606_20441_b300 import inputs  # noqa: E402
 
 METRIC = "Pauli-term updates/s"
 UNIT = "updates/s"
-PROFILE = os.path.join(ROOT, "profiles", "k_process_warp_tfim7x8.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_process_orbit_tfim7x8.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2606_20441_b300", "csrc", f)
-                  for f in ("pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh")]
+                  for f in ("pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh", "pp_orbit.cuh")]
 
 
 def workload(args):
@@ -62,12 +62,12 @@ def oracle_sample(args, steps):
     return inputs.workload_6x6(eps=args.eps, steps=steps)
 
 
-def config_of(args, inst):
+def config_of(args, inst, precision=None):
     m = inst.meta
     return {"workload": "%s_s%d_eps%g_wmax%d" % (args.workload, m["steps"], args.eps, inst.w_max),
             "lattice": "%dx%d" % (m["rows"], m["cols"]), "qubits": inst.n_qubits,
             "trotter_steps": m["steps"], "eps": args.eps, "w_max": inst.w_max,
-            "coefficients": "fp%d" % args.precision, "noise": "inverse sparse Pauli-Lindblad, "
+            "coefficients": "fp%d" % (precision or args.precision), "noise": "inverse sparse Pauli-Lindblad, "
             "3n + 9|E| generators per step", "l2": "working set (>1 GB of strings) larger than L2",
             "parallelism": "replicas"}
 
@@ -148,6 +148,26 @@ def profiled_traffic(strings_per_launch, precision, plan):
     if (int(m_plan.group(1)), float(m_plan.group(2))) != (int(plan[0]), round(float(plan[1]), 6)):
         return None
     return float(m_tr.group(1)) * strings_per_launch
+
+
+def set_difference_counts(a, b):
+    """Strings present in export a and not in b, and the reverse, from (x, z,
+    c) exports, counted on the GPU (sorted 64-bit hashes of the keys)."""
+    import torch
+
+    def hashes(e):
+        x = torch.from_numpy(np.ascontiguousarray(e[0]).view(np.int64)).cuda()
+        z = torch.from_numpy(np.ascontiguousarray(e[1]).view(np.int64)).cuda()
+        h = torch.zeros(x.shape[0], dtype=torch.int64, device="cuda")
+        for w in range(x.shape[1]):
+            h = h * 0x100000001B3 + x[:, w] * 0x1F3D5B79 + z[:, w] * 0x2545F491 + (x[:, w] ^ (z[:, w] << 7))
+        return h
+    ha, hb = hashes(a), hashes(b)
+    only_a = int((~torch.isin(ha, hb)).sum().item())
+    only_b = int((~torch.isin(hb, ha)).sum().item())
+    del ha, hb
+    torch.cuda.empty_cache()
+    return only_a, only_b
 
 
 def replica_totals(sec, updates, device):
@@ -269,10 +289,12 @@ def reference_arm(args, rank, world):
     v = upd / sec
     sample = ("%s cut to its first %d Trotter steps per timed step (warm-up steps: first 1 step); "
               "single-threaded FP64 hash-map oracle" % (args.workload, args.sample_steps))
+    cfg = config_of(args, inst, precision=64)
+    cfg["sample"] = "first %d of the %d Trotter steps per timed step" % (args.sample_steps, inst.meta["steps"])
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(args, inst), "impl": "reference",
+            "config": cfg, "impl": "reference",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -293,7 +315,7 @@ def ours_arm(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     inst = workload(args)
-    h = pp.Handle(inst.n_qubits, precision=args.precision)
+    h = pp.Handle(inst.n_qubits, precision=args.precision, timing=True)
     plan = h.pp_get_tuning()
     h.load_instance(inst)
     for _ in range(args.warmup):
@@ -358,14 +380,33 @@ def ours_arm(args, rank, world, local_rank):
         e2e_sec = float(t.item())
         e2e_upd *= world
 
-    # FP32 form against the FP64 form on the same workload (FP64 final sums in both)
-    err = None
+    # FP32 form against the FP64 form on the same workload (FP64 final sums in
+    # both): the expectation error, the strings kept by one form and not the
+    # other, the FP64 form's own speed, and how much the FP64 result moves when
+    # its threshold moves by one FP32 rounding (2^-24 relative)
+    fp32_vs_fp64 = None
     if args.precision == 32 and rank == 0 and not args.no_fp64_check:
+        keys32 = h.pp_export_terms()
         h64 = pp.Handle(inst.n_qubits, precision=64)
         h64.load_instance(inst)
+        t = time.perf_counter()
         h64.run_instance(inst)
-        err = abs(expect - h64.pp_expect())
+        e64 = h64.pp_expect()
+        sec64 = time.perf_counter() - t
+        upd64 = h64.pp_get_stats().updates
+        keys64 = h64.pp_export_terms()
+        sens = []
+        for f in (1.0 + 2.0 ** -24, 1.0 - 2.0 ** -24):
+            h64.run_instance(inst, eps=args.eps * f)
+            sens.append(h64.pp_expect() - e64)
         h64.close()
+        only32, only64 = set_difference_counts(keys32, keys64)
+        fp32_vs_fp64 = {"abs_err": abs(expect - e64), "expect_fp64": e64,
+                        "strings_only_fp32": only32, "strings_only_fp64": only64,
+                        "terms_fp32": int(len(keys32[2])), "terms_fp64": int(len(keys64[2])),
+                        "fp64_ms_per_step": 1000.0 * sec64, "fp64_updates_per_s": upd64 / sec64,
+                        "fp64_threshold_sensitivity": {"eps*(1+2^-24)": sens[0], "eps*(1-2^-24)": sens[1]}}
+        del keys32, keys64
     h.close()
 
     if rank != 0:
@@ -376,7 +417,10 @@ def ours_arm(args, rank, world, local_rank):
     main_ms_avg = tier_ms[0] / max(1, tier_launches[0])
     main_bytes = tier_strings[0] * bps / max(1, tier_launches[0])
     achieved = main_bytes / (main_ms_avg / 1000.0) / 1e9 if main_ms_avg > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "k_process_warp (tier 0: one warp per bucket, 248-string tiles)",
+    roofline = {"bound": "hbm", "limiter": "latency: issue slots and memory latency, not DRAM bandwidth "
+                "(profiles/k_process_orbit_tfim7x8.md)",
+                "kernel": "k_process_orbit (tier 0: one warp per bucket, strings grouped by orbit into dense "
+                          "coefficient blocks)",
                 "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": main_bytes, "avg_launch_ms": main_ms_avg,
@@ -400,7 +444,8 @@ def ours_arm(args, rank, world, local_rank):
             "clocks": clk, "gpu_launches": launches,
             "result": {"expect": expect, "terms": int(n_terms), "peak_terms": int(peak),
                        "updates_per_step": updates / args.steps,
-                       "fp32_abs_err_vs_fp64": err},
+                       "fp32_abs_err_vs_fp64": fp32_vs_fp64["abs_err"] if fp32_vs_fp64 else None},
+            "fp32_vs_fp64": fp32_vs_fp64,
             "tiers_ms_per_step": [m / args.steps for m in tier_ms]}
     print(json.dumps(line), flush=True)
     if dist:

@@ -57,7 +57,7 @@ typedef enum {
     PP_ERR_NOMEM = 3,     /* device allocation failed                                      */
     PP_ERR_CAPACITY = 4,  /* live terms exceeded the handle's capacity                     */
     PP_ERR_CUDA = 5,      /* a CUDA runtime call failed                                    */
-    PP_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up                            */
+    PP_ERR_TIMEOUT = 6    /* the propagation was cancelled (pp_cancel) before it finished  */
 } pp_status;
 
 enum { PP_PRECISION_FP64 = 64, PP_PRECISION_FP32 = 32 };
@@ -72,6 +72,9 @@ typedef struct {
     void (*free)(void* ptr, void* ctx);        /* matching release; NULL = cudaFree   */
     void* alloc_ctx;
     void* cuda_stream;             /* cudaStream_t to run on; NULL = the legacy default stream */
+    int timing;                    /* 1: record each processing tier's device time per
+                                      sub-layer (pp_stats.tier_ms; one CUDA event pair per
+                                      tier launch); 0 (default): tier_ms stays 0 */
 } pp_options;
 
 /* Fills *opt with defaults (FP64, automatic capacity, cudaMalloc, default stream). */
@@ -111,11 +114,32 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
  *   ox, oz [n_terms][W], oc [n_terms]; duplicate strings are summed.
  *   eps    coefficient threshold (>= 0; 0 keeps every nonzero term)
  *   w_max  Pauli-weight cap (< 0: none)
+ * The host waits for the device once per fused sub-layer (to size the next
+ * sub-layer's buckets from the live-term count); the tiers of a sub-layer and
+ * the overflow grouping run back to back on the device.
  * Synchronises the handle's stream.  Errors: PP_ERR_STATE (no circuit),
  * PP_ERR_ARG, PP_ERR_NOMEM, PP_ERR_CAPACITY (more live terms than the capacity;
  * raise pp_options.max_terms), PP_ERR_CUDA. */
 pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const uint64_t* oz,
                        const double* oc, double eps, int w_max);
+
+/* Asks the pp_propagate running on h (from another host thread) to stop.  It
+ * returns PP_ERR_TIMEOUT after the fused sub-layer in flight completes (no
+ * kernel is interrupted), the handle stays usable and holds no result.  A call
+ * that arrives after the propagation finished has no effect on later ones.
+ * This is the one call on a handle that may overlap another.  Errors:
+ * PP_ERR_ARG (null handle). */
+pp_status pp_cancel(pp_handle* h);
+
+/* Top-K truncation for the following pp_propagate calls (Sec. I.A: each
+ * intermediate result keeps at most its K largest Pauli terms).  After the
+ * input observable is merged and truncated, and after the gates of every
+ * layer, only the top_k strings of largest |c| survive; equal magnitudes are
+ * ranked by the string in export order (x words from the most significant,
+ * then z words), smallest first.  The threshold and weight rules still apply
+ * after every gate.  0 (the default) turns it off.  Errors: PP_ERR_ARG (null
+ * handle). */
+pp_status pp_set_top_k(pp_handle* h, size_t top_k);
 
 /* <0..0|O~|0..0> = sum of c over strings with no X or Y letter, of the last
  * successful pp_propagate.  Accumulated exactly in 128-bit fixed point (terms
@@ -169,6 +193,8 @@ typedef struct {
     double tier_ms[4];
     double tier_strings[4];
     double bytes_per_string;  /* bytes of one stored string (x, z words and coefficient) */
+    int orbit_launches;       /* tier-0 launches that used the orbit tiles (the rest of
+                                 tier 0 used the sparse warp tiles)                      */
 } pp_stats;
 
 pp_status pp_get_stats(const pp_handle* h, pp_stats* out);
@@ -187,6 +213,17 @@ const char* pp_last_error(const pp_handle* h);
  *                    sub-layer's observed growth, times this factor, fill one
  *                    warp tile; in [1, 16]; 0 = library default (2.4).  Larger
  *                    values mean more, emptier buckets.
+ *   first_tier       0..3: buckets start at this processing tier (0: orbit or
+ *                    sparse warp tiles, 1 and 2: CTA tiles in shared memory, 3:
+ *                    the global-memory tile); tiers below it pass every bucket
+ *                    on.  0 (default) is the fastest; the others exist so that
+ *                    tests can run every tier on small inputs.
+ *   orbit_tiles      1: class sub-layers are planned as single runs of gates
+ *                    with disjoint supports and tier 0 processes them with the
+ *                    orbit tiles (strings grouped by orbit into dense
+ *                    coefficient blocks); 0 (default): every sub-layer uses
+ *                    the sparse (hashed) warp tiles and same-signature gates
+ *                    fuse across up to four ascending segments.
  * pp_set_tuning copies *t and takes effect at the next pp_propagate.
  * Errors: PP_ERR_ARG (NULL pointer, value out of range; the handle keeps its
  * previous tuning).  pp_get_tuning writes the values in effect (defaults
@@ -194,6 +231,8 @@ const char* pp_last_error(const pp_handle* h);
 typedef struct {
     int max_fused_gates;
     double bucket_headroom;
+    int first_tier;
+    int orbit_tiles;
 } pp_tuning;
 
 pp_status pp_set_tuning(pp_handle* h, const pp_tuning* t);

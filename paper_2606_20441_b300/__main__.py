@@ -38,13 +38,15 @@ def main(argv=None) -> int:
     r.add_argument("--repeat", type=int, default=1)
     r.add_argument("--fused-gates", type=int, default=0, help="pp_set_tuning max_fused_gates (0: default)")
     r.add_argument("--headroom", type=float, default=0.0, help="pp_set_tuning bucket_headroom (0: default)")
+    r.add_argument("--first-tier", type=int, default=0, help="pp_set_tuning first_tier (0: default)")
+    r.add_argument("--orbit-tiles", action="store_true", help="pp_set_tuning orbit_tiles: orbit tiles in tier 0")
     a = ap.parse_args(argv)
 
     from . import pp
     inst = _instance(a.workload, a.eps, a.steps, a.w_max)
     h = pp.Handle(inst.n_qubits, precision=a.precision, max_terms=a.max_terms)
     h.load_instance(inst)
-    h.pp_set_tuning(a.fused_gates, a.headroom)
+    h.pp_set_tuning(a.fused_gates, a.headroom, a.first_tier, int(a.orbit_tiles))
     for _ in range(a.repeat):
         h.run_instance(inst)
     e = h.pp_expect()
@@ -53,7 +55,8 @@ def main(argv=None) -> int:
                       "expect": e, "updates": s.updates, "terms": s.n_terms, "peak_terms": s.peak_terms,
                       "tier_launches": list(s.tier_launches), "tier_ms": list(s.tier_ms),
                       "tier_strings": list(s.tier_strings), "bytes_per_string": s.bytes_per_string,
-                      "kernel_launches": s.kernel_launches, "seconds": s.seconds,
+                      "kernel_launches": s.kernel_launches, "orbit_launches": s.orbit_launches,
+                      "seconds": s.seconds,
                       "tuning": list(h.pp_get_tuning())}), flush=True)
     h.close()
     return 0

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpp.so")
 SOURCES = ["pp.cu", "pp_noalloc.cu"]
-HEADERS = ["pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh", "pp_result.cuh"]
+HEADERS = ["pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh", "pp_orbit.cuh", "pp_topk.cuh", "pp_result.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "-diag-suppress", "177"]
 

@@ -13,12 +13,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pp.h"
 #include "pp_kernels.cuh"
 #include "pp_warp.cuh"
+#include "pp_orbit.cuh"
+#include "pp_topk.cuh"
 #include "pp_result.cuh"
 
 using namespace pp;
+
+// NVTX ranges around each sub-layer's launches (visible in Nsight timelines).
+#define PP_RANGE_PUSH(name) nvtxRangePushA(name)
+#define PP_RANGE_POP() nvtxRangePop()
 
 namespace {
 
@@ -71,7 +79,7 @@ struct Arena {
 
 struct pp_handle {
     pp_options opt;
-    pp_tuning tune{0, 0.0};   // zeros select the library defaults
+    pp_tuning tune{0, 0.0, 0, 0};   // zeros select the library defaults
     int n = 0, W = 1;
     cudaStream_t st = nullptr;
     std::string err;
@@ -116,6 +124,19 @@ struct pp_handle {
     unsigned char* sort_scratch = nullptr;   // export sort: digit counts and scan sums
     size_t sort_scratch_bytes = 0;
     std::vector<void*> owned;
+
+    bool mem_ready = false;        // every work buffer below is allocated
+    std::atomic<long long> run_gen{0};       // generation of the running (or last) propagation
+    std::atomic<long long> cancel_gen{-1};   // generation pp_cancel asked to stop
+
+    // per-tier device times (pp_options.timing): one event pair per tier,
+    // reused every sub-layer
+    bool timing = false;
+    cudaEvent_t tier_ev[N_TIERS][2] = {};
+
+    // top-K truncation (0: off) and its device state
+    size_t top_k = 0;
+    TopKState* topk_state = nullptr;
 
     // result
     bool have_result = false;
@@ -234,6 +255,35 @@ double bucket_headroom(const pp_handle* h) {
     return h->tune.bucket_headroom > 0.0 ? h->tune.bucket_headroom : 2.4;
 }
 
+// Marks class sub-layers as orbit sub-layers and fills their letter table:
+// for the letters (la on a, lb on a + shift) of the orbit member whose
+// coordinate bit is 0 (x on a if the gate has an X part there, else z), the
+// sign of its sin-branch into its partner (i R P = phi P', Sec. I Eq.
+// evolve_gate) and the change of Pauli weight on the gate's sites.
+void set_orbit_table(SubLayerDesc& d) {
+    d.orb = (d.cls == CLS_NONE) || ((d.cls == CLS_LOCAL1 || d.cls == CLS_LOCAL2) && d.nseg == 1);
+    std::memset(d.ltab, 0xff, sizeof(d.ltab));
+    if (d.cls != CLS_LOCAL1 && d.cls != CLS_LOCAL2) return;
+    const int two = d.cls == CLS_LOCAL2;
+    const int ra = d.ax + 2 * d.az, rb = two ? d.bx + 2 * d.bz : 0;
+    auto anti = [](int l, int r) { return ((l & 1) & (r >> 1)) ^ ((l >> 1) & (r & 1)); };
+    auto wt = [](int l) { return l != 0 ? 1 : 0; };
+    // power of i contributed by one qubit of R * S (letter codes x + 2z)
+    auto ph = [](int r, int s) {
+        const int rx = r & 1, rz = r >> 1, sx = s & 1, sz = s >> 1;
+        return rx * rz + sx * sz + 2 * rz * sx - ((rx ^ sx) & (rz ^ sz));
+    };
+    for (int la = 0; la < 4; ++la)
+        for (int lb = 0; lb < (two ? 4 : 1); ++lb) {
+            const int cbit = d.ax ? (la & 1) : (la >> 1);
+            if (cbit || !(anti(la, ra) ^ anti(lb, rb))) continue;
+            const int e = (ph(ra, la) + (two ? ph(rb, lb) : 0)) & 3;
+            const int negphi = ((1 + e) & 3) == 0 ? 0 : 1;
+            const int dw = wt(la ^ ra) - wt(la) + (two ? wt(lb ^ rb) - wt(lb) : 0);
+            d.ltab[la + 4 * lb] = (uint8_t)(negphi | ((dw + 1) << 1));
+        }
+}
+
 // Splits a layer's gates (listed order) into fused sub-layers.
 void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int layer) {
     const int W = h->W, n = h->n;
@@ -243,7 +293,8 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
     bool open = false;
     GateSig cur_sig{};
     int last_slot = -1;
-    std::vector<bool> used(MAX_SITES, false);
+    std::vector<bool> used(MAX_SITES, false);        // sites touched by the open sub-layer's gates
+    std::vector<bool> first_used(MAX_SITES, false);  // first sites (slots) of its gates
     auto close = [&]() {
         if (open) out.push_back(cur);
         open = false;
@@ -258,6 +309,7 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
         cur_sig = s;
         last_slot = -1;
         std::fill(used.begin(), used.end(), false);
+        std::fill(first_used.begin(), first_used.end(), false);
     };
     for (int g : gates) {
         const uint64_t* rx = &h->gx[(size_t)g * W];
@@ -281,8 +333,20 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
             cur.slot_of[j] = (int16_t)j;
             continue;
         }
-        bool fits = open && cur.cls != CLS_GENERIC && cur_sig.same(s) && !used[s.slot] &&
-                    (s.slot > last_slot || cur.nseg < MAX_SEG) && cur.n_gates < max_gates;
+        // With orbit tiles, a class sub-layer is one ascending run of slots
+        // whose gates have pairwise disjoint supports: its orbits are then
+        // hypercubes with one coordinate bit per acting gate (pp_orbit.cuh).
+        // Otherwise runs of the same signature fuse across up to MAX_SEG
+        // ascending segments (e.g. both colours of horizontal R_ZZ edges).
+        bool fits;
+        if (h->tune.orbit_tiles) {
+            const bool disjoint = !used[s.slot] && (s.cls != CLS_LOCAL2 || !used[s.slot + s.shift]);
+            fits = open && cur.cls != CLS_GENERIC && cur_sig.same(s) && s.slot > last_slot && disjoint &&
+                   cur.n_gates < max_gates;
+        } else {
+            fits = open && cur.cls != CLS_GENERIC && cur_sig.same(s) && !first_used[s.slot] &&
+                   (s.slot > last_slot || cur.nseg < MAX_SEG) && cur.n_gates < max_gates;
+        }
         if (!fits) {
             close();
             start(s);
@@ -297,14 +361,18 @@ void plan_layer(pp_handle* h, const std::vector<int>& gates, int noise_idx, int 
         cur.slot_of[cur.n_gates] = (int16_t)s.slot;
         cur.n_gates++;
         used[s.slot] = true;
+        first_used[s.slot] = true;
+        if (s.cls == CLS_LOCAL2) used[s.slot + s.shift] = true;
         last_slot = s.slot;
     }
     close();
+    for (auto& d : out) set_orbit_table(d);
     if (out.empty() && noise_idx >= 0) {
         SubLayerDesc d;
         std::memset(&d, 0, sizeof(d));
         d.cls = CLS_NONE;
         d.noise = -1;
+        set_orbit_table(d);
         out.push_back(d);
     }
     if (!out.empty()) out[0].noise = noise_idx;
@@ -383,15 +451,30 @@ pp_status build_plan(pp_handle* h) {
     h->sub_kind.clear();
     std::vector<std::vector<int>> by_layer(h->n_layers);
     for (size_t g = 0; g < h->theta.size(); ++g) by_layer[h->layer_of[g]].push_back((int)g);
+    if (h->top_k > 0) {
+        // the input observable gets its own pass (merge, truncation), so that
+        // top-K can act on it before the first gate
+        SubLayerDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.cls = CLS_NONE;
+        d.noise = -1;
+        d.layer_end = 1;
+        set_orbit_table(d);
+        h->subs.push_back(d);
+        h->sub_kind.push_back(0);
+    }
     for (int l = h->n_layers - 1; l >= 0; --l) {
         int nz = h->noise.count(l) ? l : -1;
+        const size_t before = h->subs.size();
         plan_layer(h, by_layer[l], nz, l);
+        if (h->subs.size() > before) h->subs.back().layer_end = 1;
     }
     if (h->subs.empty()) {
         SubLayerDesc d;
         std::memset(&d, 0, sizeof(d));
         d.cls = CLS_NONE;
         d.noise = -1;
+        set_orbit_table(d);
         h->subs.push_back(d);
         h->sub_kind.push_back(0);
     }
@@ -434,8 +517,58 @@ pp_status alloc_arena(pp_handle* h, Arena* a, size_t cap) {
     return PP_OK;
 }
 
+// Releases every work buffer of the handle (not its table arena) and resets
+// the pointers, so that a failed set-up leaves the handle as it was created.
+void release_work_memory(pp_handle* h) {
+    auto rel = [&](auto*& ptr) {
+        if (ptr) dev_free(h, (void*)ptr);
+        ptr = nullptr;
+    };
+    for (Arena* a : {&h->arena[0], &h->arena[1], &h->spill_raw, &h->spill_grp}) {
+        rel(a->x);
+        rel(a->z);
+        rel(a->c);
+    }
+    rel(h->spill_b);
+    rel(h->spill_s);
+    rel(h->spill_ctr);
+    for (int s = 0; s < 2; ++s) {
+        rel(h->fill[s]);
+        rel(h->soff[s]);
+    }
+    rel(h->counters);
+    rel(h->delta);
+    for (auto& l : h->pass_list) rel(l);
+    rel(h->partial);
+    rel(h->topk_state);
+    rel(h->fb_scratch);
+    rel(h->stage);
+    rel(h->sort_scratch);
+    h->stage_cap = 0;
+    h->sort_scratch_bytes = 0;
+    h->mem_ready = false;
+}
+
+pp_status ensure_memory_once(pp_handle* h);
+
+// Work buffers, allocated at the first propagation.  All or nothing: when an
+// allocation fails, the ones made so far are released and PP_ERR_NOMEM is
+// returned with the handle unchanged, so a later call can try again.
 pp_status ensure_memory(pp_handle* h) {
-    if (h->arena[0].x) return PP_OK;
+    if (h->mem_ready) return PP_OK;
+    pp_status st = ensure_memory_once(h);
+    if (st != PP_OK) {
+        cudaStreamSynchronize(h->st);
+        std::string msg = h->err;
+        release_work_memory(h);
+        h->err = msg;
+        return st;
+    }
+    h->mem_ready = true;
+    return PP_OK;
+}
+
+pp_status ensure_memory_once(pp_handle* h) {
     size_t tb = term_bytes(h);
     size_t cap = h->opt.max_terms;
     if (cap == 0) {
@@ -468,9 +601,11 @@ pp_status ensure_memory(pp_handle* h) {
         if (!(h->pass_list[k] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap))))
             return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * (4096 + 1)));
+    h->topk_state = static_cast<TopKState*>(dev_alloc(h, sizeof(TopKState)));
+    if (!h->topk_state) return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     if (!h->spill_b || !h->spill_s || !h->counters || !h->delta || !h->partial)
         return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
-    return PP_OK;
+    return ensure_global_tier(h);
 }
 
 // Smallest power of two >= v, but at most the largest power of two <= cap.
@@ -480,50 +615,93 @@ uint32_t pow2_at_least(double v, uint32_t cap) {
     return b;
 }
 
+// Per-device launch facts of one kernel: the dynamic shared-memory limit set
+// on it and its resident CTAs per SM.  Both are properties of the device the
+// handle runs on, so they are kept per device ordinal; the occupancy query is
+// made once per device (it takes driver locks that concurrent handles share).
+struct KernelFacts {
+    static constexpr int kDevices = 64;
+    std::atomic<size_t> attr[kDevices];
+    std::atomic<int> occ[kDevices];
+    KernelFacts() {
+        for (int i = 0; i < kDevices; ++i) {
+            attr[i].store(0);
+            occ[i].store(0);
+        }
+    }
+};
+
+template <typename K>
+cudaError_t prepare_kernel(const pp_handle* h, KernelFacts& f, K kernel, int threads, size_t smem, int* per_sm) {
+    const int dev = h->device;
+    if (dev < 0 || dev >= KernelFacts::kDevices) return cudaErrorInvalidDevice;
+    if (f.attr[dev].load() < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        f.attr[dev].store(smem);
+    }
+    int n = f.occ[dev].load();
+    if (n == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
+        if (e != cudaSuccess) return e;
+        n = std::max(n, 1);
+        f.occ[dev].store(n);
+    }
+    *per_sm = n;
+    return cudaSuccess;
+}
+
 template <int W, typename T, int NT>
 cudaError_t launch_smem_tier(pp_handle* h, const StepParams& p, int cap, uint32_t n_items) {
     const size_t smem = tile_layout_bytes<W, T, int16_t>((size_t)cap);
-    static std::atomic<size_t> attr_set(0);   // shared by the threads of pp_propagate_batch
-    if (attr_set.load() < smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_process<W, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set.store(smem);
-    }
-    // resident CTAs per SM: a property of the kernel and its shared memory,
-    // queried once (the query takes driver locks that concurrent handles share)
-    static std::atomic<int> occ(0);
-    int per_sm = occ.load();
-    if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process<W, T, NT>, NT, smem);
-        per_sm = std::max(per_sm, 1);
-        occ.store(per_sm);
-    }
+    static KernelFacts facts;   // shared by the threads of pp_propagate_batch
+    int per_sm = 1;
+    cudaError_t e = prepare_kernel(h, facts, k_process<W, T, NT>, NT, smem, &per_sm);
+    if (e != cudaSuccess) return e;
     uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(per_sm * h->sm_count));
     k_process<W, T, NT><<<grid, NT, smem, h->st>>>(p, cap);
     return cudaGetLastError();
 }
 
+// Tile capacities of the orbit tier: strings per bucket, orbit hash slots,
+// pool slots, round records.  PP_ORBIT_CAPS="O,H,M,S" overrides them for
+// measurements.
 template <int W, typename T>
-cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t n_items, int* launches) {
+OrbCaps orbit_caps() {
+    OrbCaps k{128, 256, 1024, 512};
+    if (const char* e = getenv("PP_ORBIT_CAPS")) {
+        OrbCaps v{};
+        if (sscanf(e, "%d,%d,%d,%d", &v.O, &v.H, &v.M, &v.S) == 4 && v.O > 0 && v.O <= 4096 && v.H >= 2 * v.O &&
+            (v.H & (v.H - 1)) == 0 && v.M >= 64 && v.M <= 65536 && v.S > 0 && v.S <= 65535)
+            k = v;
+    }
+    return k;
+}
+
+template <int W, typename T>
+cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orbit, uint32_t n_items,
+                           int* launches) {
     ++*launches;
     const int cap = W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2;
     switch (tier) {
         case 0: {
-            const size_t smem = warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS;
-            static std::atomic<size_t> attr_set(0);
-            if (attr_set.load() < smem) {
-                cudaError_t e = cudaFuncSetAttribute(k_process_warp<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)smem);
+            if (orbit) {
+                const OrbCaps K = orbit_caps<W, T>();
+                const size_t smem = orb_layout<W, T>(K).bytes * ORB_WARPS;
+                static KernelFacts facts;
+                int per_sm = 1;
+                cudaError_t e = prepare_kernel(h, facts, k_process_orbit<W, T>, 32 * ORB_WARPS, smem, &per_sm);
                 if (e != cudaSuccess) return e;
-                attr_set.store(smem);
+                uint32_t grid = std::min<uint32_t>(std::max<uint32_t>((n_items + ORB_WARPS - 1) / ORB_WARPS, 1),
+                                                   (uint32_t)(per_sm * h->sm_count));
+                k_process_orbit<W, T><<<grid, 32 * ORB_WARPS, smem, h->st>>>(p, K);
+                return cudaGetLastError();
             }
-            static std::atomic<int> occ(0);   // as in launch_smem_tier
-            int per_sm = occ.load();
-            if (per_sm == 0) {
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_process_warp<W, T>, kTiers[0].threads, smem);
-                per_sm = std::max(per_sm, 1);
-                occ.store(per_sm);
-            }
+            const size_t smem = warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS;
+            static KernelFacts facts;
+            int per_sm = 1;
+            cudaError_t e = prepare_kernel(h, facts, k_process_warp<W, T>, kTiers[0].threads, smem, &per_sm);
+            if (e != cudaSuccess) return e;
             uint32_t grid = std::min<uint32_t>(std::max<uint32_t>((n_items + WARP_TILE_WARPS - 1) / WARP_TILE_WARPS, 1),
                                                (uint32_t)(per_sm * h->sm_count));
             k_process_warp<W, T><<<grid, kTiers[0].threads, smem, h->st>>>(p, cap);
@@ -542,12 +720,19 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, uint32_t
 
 int tier_cap(const pp_handle* h, int tier) { return h->W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2; }
 
-cudaError_t dispatch_process(pp_handle* h, const StepParams& p, int tier, uint32_t n_items, int* launches) {
+cudaError_t dispatch_process(pp_handle* h, const StepParams& p, int tier, bool orbit, uint32_t n_items,
+                             int* launches) {
     bool f32 = h->opt.precision == PP_PRECISION_FP32;
-    if (h->W == 1) return f32 ? launch_process<1, float>(h, p, tier, n_items, launches)
-                              : launch_process<1, double>(h, p, tier, n_items, launches);
-    return f32 ? launch_process<2, float>(h, p, tier, n_items, launches)
-               : launch_process<2, double>(h, p, tier, n_items, launches);
+    if (h->W == 1) return f32 ? launch_process<1, float>(h, p, tier, orbit, n_items, launches)
+                              : launch_process<1, double>(h, p, tier, orbit, n_items, launches);
+    return f32 ? launch_process<2, float>(h, p, tier, orbit, n_items, launches)
+               : launch_process<2, double>(h, p, tier, orbit, n_items, launches);
+}
+
+// Load limit of a bucket of the orbit tier.
+int orbit_load_cap(const pp_handle* h) {
+    if (h->W == 1) return h->opt.precision == PP_PRECISION_FP32 ? orbit_caps<1, float>().O : orbit_caps<1, double>().O;
+    return h->opt.precision == PP_PRECISION_FP32 ? orbit_caps<2, float>().O : orbit_caps<2, double>().O;
 }
 
 cudaError_t dispatch_scatter(pp_handle* h, const uint64_t* ox, const uint64_t* oz, const double* oc,
@@ -611,24 +796,15 @@ cudaError_t apply_noise(pp_handle* h, const NoiseHost& nh, int side, uint32_t B,
     return cudaGetLastError();
 }
 
-// Strings in the overflow area after a launch (sum over its shards).
-cudaError_t spill_total(pp_handle* h, unsigned long long* total) {
-    unsigned long long f[NSPILL];
-    cudaError_t e = cudaMemcpyAsync(f, h->spill_ctr, sizeof(f), cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    *total = 0;
-    for (int i = 0; i < NSPILL; ++i) *total += f[i];
-    return e;
-}
-
-// Groups the overflow strings of a freshly written layout by bucket.
-cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, uint64_t n_spill, int* launches) {
-    if (n_spill == 0) return cudaSuccess;
+// Groups the overflow strings of a freshly written layout by bucket.  Runs
+// whether or not anything spilled (the kernels find out on the device); the
+// number of grouped strings lands in counters[CTR_SPILL_TOTAL].
+cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, int* launches) {
     cudaError_t e = cudaMemsetAsync(h->counters + CTR_SPILL_TOTAL, 0, sizeof(unsigned long long), h->st);
     if (e != cudaSuccess) return e;
     uint32_t grid = (nB + 1023) / 1024;
     k_spill_offsets<<<grid, 1024, 0, h->st>>>(h->fill[side], nB, C, h->soff[side], h->counters + CTR_SPILL_TOTAL);
-    int g2 = (int)std::min<uint64_t>((h->spill_cap + 255) / 256, 16384);
+    const dim3 g2(NSPILL, (unsigned)std::max(1, h->sm_count * 8 / NSPILL));
     const bool f32 = h->opt.precision == PP_PRECISION_FP32;
     const Arena& r = h->spill_raw;
     const Arena& o = h->spill_grp;
@@ -653,6 +829,71 @@ float eps_float_ceil(double eps) {
 }  // namespace
 
 namespace {
+
+// Keeps the K largest live strings of a span (pp_topk.cuh); the rest get
+// coefficient 0.  Every decision stays on the device.
+template <int W, typename T>
+cudaError_t top_k_span(pp_handle* h, const Span<T>& s, size_t K, int* launches) {
+    TopKState* st = h->topk_state;
+    const int grid = h->sm_count * 4;
+    k_topk_init<<<1, 256, 0, h->st>>>(st, (unsigned long long)K);
+    for (int shift = MagBits<T>::BITS - 8; shift >= 0; shift -= 8) {
+        k_topk_hist<W, T><<<grid, 256, 0, h->st>>>(s, st, shift);
+        k_topk_pick<<<1, 256, 0, h->st>>>(st, shift, shift == 0);
+        *launches += 2;
+    }
+    for (int kw = 0; kw < 2 * W; ++kw)
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            k_topk_key_hist<W, T><<<grid, 256, 0, h->st>>>(s, st, kw, shift);
+            k_topk_key_pick<<<1, 256, 0, h->st>>>(st, kw, shift);
+            *launches += 2;
+        }
+    k_topk_mark<W, T><<<grid, 256, 0, h->st>>>(s, st);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+// Top-K on layout `side` (B buckets of C, n_over grouped overflow strings), or
+// on the compact result [0, n_over) of `side` when fill is false.
+cudaError_t apply_top_k(pp_handle* h, int side, bool bucketed, uint32_t B, uint64_t C, uint64_t n_over,
+                        int* launches) {
+    const Arena& a = h->arena[side];
+    const Arena& o = bucketed ? h->spill_grp : a;
+    const uint64_t ocap = bucketed ? h->spill_cap : h->cap;
+    const uint32_t* fill = bucketed ? h->fill[side] : nullptr;
+#define PP_TOPK(WW, TT)                                                                                 \
+    {                                                                                                   \
+        Span<TT> s{a.x, a.z, (TT*)a.c, h->cap, fill, B, C, o.x, o.z, (TT*)o.c, ocap, n_over};         \
+        return top_k_span<WW, TT>(h, s, h->top_k, launches);                                          \
+    }
+    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    if (h->W == 1) {
+        if (f32) PP_TOPK(1, float) else PP_TOPK(1, double)
+    } else {
+        if (f32) PP_TOPK(2, float) else PP_TOPK(2, double)
+    }
+#undef PP_TOPK
+}
+
+// Compacts the live strings of the result [0, n) on `side` into the other arena.
+cudaError_t compact_result(pp_handle* h, int side, uint64_t n, int* launches) {
+    const Arena& a = h->arena[side];
+    const Arena& d = h->arena[side ^ 1];
+    unsigned long long* cnt = h->counters + CTR_SPILL_TOTAL;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), h->st);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<uint64_t>(std::max<uint64_t>((n + 255) / 256, 1), (uint64_t)h->sm_count * 8);
+    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    if (h->W == 1) {
+        if (f32) k_compact<1, float><<<grid, 256, 0, h->st>>>(a.x, a.z, (const float*)a.c, h->cap, n, d.x, d.z, (float*)d.c, h->cap, cnt);
+        else k_compact<1, double><<<grid, 256, 0, h->st>>>(a.x, a.z, (const double*)a.c, h->cap, n, d.x, d.z, (double*)d.c, h->cap, cnt);
+    } else {
+        if (f32) k_compact<2, float><<<grid, 256, 0, h->st>>>(a.x, a.z, (const float*)a.c, h->cap, n, d.x, d.z, (float*)d.c, h->cap, cnt);
+        else k_compact<2, double><<<grid, 256, 0, h->st>>>(a.x, a.z, (const double*)a.c, h->cap, n, d.x, d.z, (double*)d.c, h->cap, cnt);
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
 
 // Orders the result's strings by key on the device (pp_result.cuh): radix
 // passes ping-pong between the two term arenas; the sorted result stays the
@@ -726,6 +967,7 @@ pp_status pp_create(const pp_options* opt, int n_qubits, pp_handle** out) {
     if (h->opt.precision != PP_PRECISION_FP32) h->opt.precision = PP_PRECISION_FP64;
     h->n = n_qubits;
     h->W = (n_qubits + 63) / 64;
+    h->timing = h->opt.timing != 0;
     h->st = static_cast<cudaStream_t>(h->opt.cuda_stream);
     h->device = 0;
     int dev = 0;
@@ -745,6 +987,9 @@ pp_status pp_destroy(pp_handle* h) {
     cudaStreamSynchronize(h->st);
     std::vector<void*> all = h->owned;
     for (void* p : all) dev_free(h, p);
+    for (auto& pr : h->tier_ev)
+        for (auto& e : pr)
+            if (e) cudaEventDestroy(e);
     delete h;
     return PP_OK;
 }
@@ -758,8 +1003,24 @@ pp_status pp_set_tuning(pp_handle* h, const pp_tuning* t) {
         return fail(h, PP_ERR_ARG, "max_fused_gates must be 0 (default) or 1..64*W");
     if (t->bucket_headroom != 0.0 && !(t->bucket_headroom >= 1.0 && t->bucket_headroom <= 16.0))
         return fail(h, PP_ERR_ARG, "bucket_headroom must be 0 (default) or in [1, 16]");
-    if (t->max_fused_gates != h->tune.max_fused_gates) h->subs_dirty = true;
+    if (t->first_tier < 0 || t->first_tier >= N_TIERS) return fail(h, PP_ERR_ARG, "first_tier must be in 0..3");
+    if (t->orbit_tiles != 0 && t->orbit_tiles != 1) return fail(h, PP_ERR_ARG, "orbit_tiles must be 0 or 1");
+    if (t->max_fused_gates != h->tune.max_fused_gates || t->orbit_tiles != h->tune.orbit_tiles) h->subs_dirty = true;
     h->tune = *t;
+    return PP_OK;
+}
+
+pp_status pp_cancel(pp_handle* h) {
+    if (!h) return PP_ERR_ARG;
+    h->cancel_gen.store(h->run_gen.load());
+    return PP_OK;
+}
+
+pp_status pp_set_top_k(pp_handle* h, size_t top_k) {
+    if (!h) return PP_ERR_ARG;
+    h->err.clear();
+    if (top_k != h->top_k) h->subs_dirty = true;
+    h->top_k = top_k;
     return PP_OK;
 }
 
@@ -767,6 +1028,8 @@ pp_status pp_get_tuning(const pp_handle* h, pp_tuning* t) {
     if (!h || !t) return PP_ERR_ARG;
     t->max_fused_gates = max_fused_gates(h);
     t->bucket_headroom = bucket_headroom(h);
+    t->first_tier = h->tune.first_tier;
+    t->orbit_tiles = h->tune.orbit_tiles;
     return PP_OK;
 }
 
@@ -934,6 +1197,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     if (n_terms && (!ox || !oz || !oc)) return fail(h, PP_ERR_ARG, "null observable arrays");
     if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(h, PP_ERR_ARG, "eps must be finite and >= 0");
     h->have_result = false;
+    const long long gen = ++h->run_gen;
     pp_status st;
     if (h->subs_dirty && (st = build_plan(h)) != PP_OK) return st;
     if ((st = ensure_memory(h)) != PP_OK) return st;
@@ -961,11 +1225,8 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
 
     struct Scope {
         FILE* trace = nullptr;
-        cudaEvent_t ev[2] = {nullptr, nullptr};
         ~Scope() {
             if (trace) fclose(trace);
-            for (auto e : ev)
-                if (e) cudaEventDestroy(e);
         }
     } scope;
     if (const char* tp = getenv("PP_TRACE")) scope.trace = fopen(tp, "a");
@@ -974,7 +1235,9 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     if (trace) {
         phase = h->counters + CTR_PHASE;
     }
-    for (auto& e : scope.ev) CK(cudaEventCreate(&e));
+    if (h->timing && !h->tier_ev[0][0])
+        for (auto& pr : h->tier_ev)
+            for (auto& e : pr) CK(cudaEventCreate(&e));
 
     const size_t tcap = (size_t)tier_cap(h, 0);
     std::map<int, double> growth;   // observed output/input per sub-layer kind
@@ -985,8 +1248,19 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     // buckets for sub-layer s holding about n strings: its tile must also hold
     // the strings the sub-layer creates, so aim at tcap / (headroom * growth)
     const double headroom = bucket_headroom(h);
+    // sub-layers processed by the orbit tier first (the input observable, which
+    // may hold duplicates, and sub-layers after a forced first tier go to the
+    // sparse tiers)
+    auto use_orbit = [&](int s) {
+        const SubLayerDesc& d = h->subs[s];
+        return d.orb && !d.first && h->tune.orbit_tiles && h->tune.first_tier == 0;
+    };
+    // an orbit bucket holds its input strings; the strings it creates live in
+    // its coefficient pool, so only the input is planned (at 3/4 of the limit)
+    const double ocap = 0.75 * orbit_load_cap(h);
     auto buckets_for = [&](int s, double n) {
-        double per = (double)tcap / (headroom * std::max(1.0, growth_of(s)));
+        const double g = headroom * std::max(1.0, growth_of(s));
+        double per = use_orbit(s) ? ocap : (double)tcap / g;
         per = std::max(per, 16.0);
         return pow2_at_least(n / per, h->fill_cap);
     };
@@ -1016,6 +1290,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     uint32_t B = buckets_for(0, (double)n_terms);
     uint64_t C = h->cap / B;
     unsigned long long ctr[CTR_COUNT];
+    long long dl[MAX_SITES];
     CK(cudaMemsetAsync(h->fill[side], 0, sizeof(uint32_t) * B, h->st));
     CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
     CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
@@ -1028,14 +1303,16 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     p.dC = C;
     p.next = h->d_subs;
     if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, p, &launches));
+    CK(group_spill(h, side, B, C, &launches));
     CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input overflowed the overflow area");
-    unsigned long long n_spill = 0;
-    CK(spill_total(h, &n_spill));
-    CK(group_spill(h, side, B, C, n_spill, &launches));
-    unsigned long long n_over_in = n_spill;   // grouped overflow strings of the current layout
+    unsigned long long n_over_in = ctr[CTR_SPILL_TOTAL];   // grouped overflow strings of the current layout
 
+    // One host synchronisation per sub-layer: the tiers after the first read
+    // their work counts from the device (the previous tier's deferral
+    // counter), the overflow grouping always runs, and the counters come back
+    // in one copy at the end.
     size_t N = n_terms;
     size_t peak = N;
     double updates = 0.0;
@@ -1047,6 +1324,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         double est = std::max(64.0, (double)N * growth_of(s) * 1.3);
         const uint32_t nB = fin ? 1 : buckets_for(s + 1, est);
         const uint64_t nC = fin ? h->cap : h->cap / nB;
+        PP_RANGE_PUSH("pp sub-layer");
         if (!fin) CK(cudaMemsetAsync(h->fill[side ^ 1], 0, sizeof(uint32_t) * nB, h->st));
         CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
         CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
@@ -1075,35 +1353,37 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
         if (d.noise >= 0 && !d.first)
             CK(apply_noise(h, h->noise[d.noise], side, B, C, n_over_in, p.eps, p.eps_f, &launches));
-        float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
-        unsigned long long passed[N_TIERS] = {0, 0, 0, 0};   // buckets tier t handed to t+1
         for (int tier = 0; tier < N_TIERS; ++tier) {
-            uint32_t n_items;
-            if (tier == 0) {
-                p.in_list = nullptr;
-                n_items = B;
-            } else {
-                n_items = (uint32_t)passed[tier - 1];
-                if (n_items == 0) break;
-                p.in_list = h->pass_list[tier - 1];
-            }
-            p.n_list = n_items;
+            p.in_list = tier == 0 ? nullptr : h->pass_list[tier - 1];
+            p.n_list = 0;
+            p.n_list_dev = tier == 0 ? nullptr : h->counters + CTR_DEFER + tier - 1;
+            const uint32_t n_items = tier == 0 ? B : UINT32_MAX;   // launch bound; the count is on the device
             p.out_list = tier < kGlobalTier ? h->pass_list[tier] : nullptr;
             p.work_ctr = CTR_WORK + tier;
             p.defer_ctr = CTR_DEFER + (tier < kGlobalTier ? tier : 0);
-            if (tier == kGlobalTier && (st = ensure_global_tier(h)) != PP_OK) return st;
+            const bool orbit = tier == 0 && use_orbit(s);
             p.max_load = (uint32_t)((tier == kGlobalTier ? h->fb_cap : tier_cap(h, tier)) * 3 / 4);
-            CK(cudaEventRecord(scope.ev[0], h->st));
-            CK(dispatch_process(h, p, tier, n_items, &launches));
-            CK(cudaEventRecord(scope.ev[1], h->st));
-            CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
-            CK(cudaStreamSynchronize(h->st));
-            cudaEventElapsedTime(&ms[tier], scope.ev[0], scope.ev[1]);
+            if (orbit) p.max_load = (uint32_t)orbit_load_cap(h);
+            if (tier < h->tune.first_tier) p.max_load = 0;   // every bucket is passed on
+            if (h->timing) CK(cudaEventRecord(h->tier_ev[tier][0], h->st));
+            CK(dispatch_process(h, p, tier, orbit, n_items, &launches));
+            if (h->timing) CK(cudaEventRecord(h->tier_ev[tier][1], h->st));
+            if (orbit) stats.orbit_launches++;
             stats.tier_launches[tier]++;
+        }
+        if (!fin) CK(group_spill(h, side ^ 1, nB, nC, &launches));
+        CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(dl, h->delta, sizeof(dl), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        PP_RANGE_POP();
+        if (h->cancel_gen.load() == gen) return fail(h, PP_ERR_TIMEOUT, "cancelled after sub-layer %d", s);
+        float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
+        for (int tier = 0; tier < N_TIERS; ++tier) {
+            if (h->timing) CK(cudaEventElapsedTime(&ms[tier], h->tier_ev[tier][0], h->tier_ev[tier][1]));
             stats.tier_ms[tier] += ms[tier];
             stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];
-            if (tier < kGlobalTier) passed[tier] = ctr[CTR_DEFER + tier];
         }
+        unsigned long long passed[N_TIERS] = {ctr[CTR_DEFER], ctr[CTR_DEFER + 1], ctr[CTR_DEFER + 2], 0};
         stats.fallback_buckets += (int)passed[kGlobalTier - 1];
         if (ctr[CTR_ERR_FALLBACK])
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s,
@@ -1112,37 +1392,45 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
                         "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap,
                         h->spill_cap);
-        unsigned long long n_spill_out = 0;
-        if (!fin) {
-            CK(spill_total(h, &n_spill_out));
-            CK(group_spill(h, side ^ 1, nB, nC, n_spill_out, &launches));
-        }
-        long long dl[MAX_SITES];
-        CK(cudaMemcpyAsync(dl, h->delta, sizeof(dl), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        // canonical gate-by-gate count: live terms entering each gate in listed order
+        const unsigned long long n_spill_out = fin ? 0ull : ctr[CTR_SPILL_TOTAL];
+        // canonical gate-by-gate count: live terms entering each gate in listed
+        // order, from the sparse tiers' per-gate births and deaths, plus the
+        // lifetimes the orbit tier summed itself
         double live = (double)ctr[CTR_PROLOGUE];
         for (int j = 0; j < d.n_gates; ++j) {
             updates += live;
             live += (double)dl[j];
         }
-        const size_t Nout = (size_t)ctr[CTR_OUT];
+        updates += (double)ctr[CTR_UPDATES];
+        size_t Nout = (size_t)ctr[CTR_OUT];
+        peak = std::max(peak, Nout);
+        bool compacted = false;
+        if (h->top_k > 0 && d.layer_end && Nout > h->top_k) {
+            // keep the K largest strings of the layer's result (Sec. I.A)
+            if (!fin) {
+                CK(apply_top_k(h, side ^ 1, true, nB, nC, n_spill_out, &launches));
+            } else {
+                CK(apply_top_k(h, side ^ 1, false, 1, h->cap, Nout, &launches));
+                CK(compact_result(h, side ^ 1, Nout, &launches));
+                compacted = true;
+            }
+            Nout = h->top_k;
+        }
         if (trace)
             fprintf(trace,
-                    "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"n_in\": %zu, \"n_out\": %zu, "
+                    "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"orbit\": %d, \"n_in\": %zu, \"n_out\": %zu, "
                     "\"buckets_in\": %u, \"buckets_out\": %u, \"passed\": [%llu, %llu, %llu], "
                     "\"spill\": %llu, \"ms\": [%.4f, %.4f, %.4f, %.4f], "
                     "\"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
                     "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu]}\n",
-                    s, d.cls, d.n_gates, N, Nout, B, nB, passed[0], passed[1], passed[2],
+                    s, d.cls, d.n_gates, (int)use_orbit(s), N, Nout, B, nB, passed[0], passed[1], passed[2],
                     n_spill_out, ms[0], ms[1], ms[2], ms[3], ctr[CTR_FAIL], ctr[CTR_FAIL + 1],
                     ctr[CTR_FAIL + 2], ctr[CTR_PHASE], ctr[CTR_PHASE + 1], ctr[CTR_PHASE + 2], ctr[CTR_PHASE + 3],
                     ctr[CTR_PHASE_CTA], ctr[CTR_PHASE_CTA + 1], ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3]);
         if (N > 0) growth[kind] = std::max(0.05, (double)Nout / (double)N);
         N = Nout;
-        peak = std::max(peak, N);
         n_over_in = n_spill_out;
-        side ^= 1;
+        if (!compacted) side ^= 1;   // a compacted result went back to this sub-layer's source arena
         B = nB;
         C = nC;
         stats.n_sublayers++;

@@ -50,7 +50,15 @@ struct SubLayerDesc {
     int noise;                    // index of the noise map applied before the gates, or -1
     int first;                    // 1: input observable (merge duplicates, truncate)
     int final_;                   // 1: last sub-layer (outputs go to the compact result)
-    int pad_;
+    int layer_end;                // 1: last sub-layer of a circuit layer (top-K applies after it)
+    int orb;                      // 1: one letter pattern, one ascending segment, disjoint
+                                  //    supports: the orbit tier may process it (pp_orbit.cuh)
+    // Orbit sub-layers: for the letters (la, lb) (code x + 2z) that the member
+    // with coordinate bit 0 carries on a gate's sites (a, a + shift), entry
+    // la + 4 lb holds bit 0: the sign of its sin-branch into its partner is
+    // negative; bits 1-2: weight(partner) - weight(member) + 1 on those sites.
+    // 0xff marks letter pairs that commute with the gate.
+    uint8_t ltab[16];
     uint64_t seg[MAX_SEG][MAXW];
     uint64_t all[MAXW];           // union of segments
     double cs[MAX_SITES];         // cos(theta) by slot
@@ -394,8 +402,9 @@ __device__ __forceinline__ int64_t noise_exponent(const NoiseDesc& nz, const uin
 // exp(+-2 s) for s = S * 2^-56 (S >= 0), as the product over the bytes of S of
 // host-tabulated factors: exp(a + b) = exp(a) exp(b), so at most seven FP64
 // multiplies instead of an FP64 exponential.  Each table entry is the exponential
-// correctly rounded to double; the product carries at most a few ulp.
-__device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t S, double) {
+// correctly rounded to double; the product carries at most a few ulp.  Both
+// coefficient precisions use it: the FP32 form rounds c * f once (Coef::scale).
+__device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t S) {
     uint64_t u = (uint64_t)S;
     double f = 1.0;
 #pragma unroll
@@ -406,19 +415,14 @@ __device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t S, d
     return f;
 }
 
-// FP32 form: the exponential in single precision (the coefficient is stored in
-// single precision anyway); the exponent itself stays exact.
-__device__ __forceinline__ float noise_factor(const NoiseDesc& nz, int64_t S, float) {
-    const float s2 = __ll2float_rn((long long)S) * 0x1p-55f;   // 2 s
-    return nz.mode == 0 ? expf(s2) : expf(-s2);
-}
-
 // ----------------------------------------------------------------------------- coefficient ops
 
 template <typename T> struct Coef;
 
 template <> struct Coef<double> {
     __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    // c times a noise factor
+    __device__ static __forceinline__ double scale(double c, double f) { return __dmul_rn(c, f); }
     __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     // cs*c + phi*(sn*c2): exactly the oracle's two contributions, no fused multiply-add
     __device__ static __forceinline__ double rot(double cs, double c, double sn, double c2, int phi) {
@@ -435,6 +439,10 @@ template <> struct Coef<double> {
 
 template <> struct Coef<float> {
     __device__ static __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    // c times a noise factor, in FP64, rounded once to float
+    __device__ static __forceinline__ float scale(float c, double f) {
+        return __double2float_rn(__dmul_rn((double)c, f));
+    }
     __device__ static __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     // Compensated cs*c + phi*sn*c2: error-free products (FMA residuals) and an
     // error-free sum, folded into one final rounding (Ogita-Rump-Oishi Dot2).

@@ -54,6 +54,8 @@ struct StepParams {
     long long* delta;             // [MAX_SITES] net change of live terms by listed gate
     const uint32_t* in_list;      // buckets to process (nullptr: all of 0..sB-1)
     uint32_t n_list;
+    const unsigned long long* n_list_dev;   // when set, in_list's length is read here (the
+                                            // previous tier's deferral counter) on the device
     uint32_t* out_list;           // buckets this tier could not hold (nullptr: report failure)
     int work_ctr;                 // counter index of this launch's work queue
     int defer_ctr;                // counter index of out_list's length
@@ -76,8 +78,16 @@ enum {
     CTR_SPILL_TOTAL = 24,// scratch of the overflow grouping
     CTR_PHASE = 28,      // tier-0 cycles per phase when tracing (28..31)
     CTR_PHASE_CTA = 32,  // CTA-tier cycles per phase when tracing (32..35)
-    CTR_COUNT = 36
+    CTR_UPDATES = 36,    // canonical work count of the buckets the orbit tier completed
+    CTR_COUNT = 37
 };
+
+// Number of work items (buckets) of a tier launch.
+__device__ __forceinline__ uint32_t work_items(const StepParams& p) {
+    if (!p.in_list) return p.sB;
+    if (p.n_list_dev) return (uint32_t)*(volatile const unsigned long long*)p.n_list_dev;
+    return p.n_list;
+}
 
 constexpr int N_TIERS = 4;
 constexpr int NSPILL = 64;   // shards of the overflow area (one atomic counter each)
@@ -323,8 +333,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                 if (Coef<T>::small(c, eps) || (p.w_max >= 0 && weight_of<W>(x, z) > p.w_max)) c = T(0);
             }
             if (p.has_noise && c != T(0)) {
-                const T f = noise_factor(p.noise, noise_exponent<W>(p.noise, x, z), T(0));
-                c = Coef<T>::mul(c, f);
+                c = Coef<T>::scale(c, noise_factor(p.noise, noise_exponent<W>(p.noise, x, z)));
                 if (Coef<T>::small(c, eps)) c = T(0);
             }
             t.c[i] = c;
@@ -635,7 +644,7 @@ __global__ void __launch_bounds__(NT) k_process(StepParams p, int cap) {
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
     if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
     load_gate_table<W, T>(tab, *p.desc);
-    const uint32_t n_items = p.in_list ? p.n_list : p.sB;
+    const uint32_t n_items = work_items(p);
     for (;;) {
         if (threadIdx.x == 0) s_b = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);
         __syncthreads();
@@ -672,11 +681,12 @@ __global__ void __launch_bounds__(NWARPS * 32) k_process_global(StepParams p, un
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
     if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
     load_gate_table<W, T>(tab, *p.desc);
+    const uint32_t n_items = work_items(p);
     for (;;) {
         if (threadIdx.x == 0) s_k = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);
         __syncthreads();
         const uint32_t k = s_k;
-        if (k >= p.n_list) break;
+        if (k >= n_items) break;
         bool ok = process_bucket<W, T, int32_t>(t, tab, s_ad, s_adn, p, p.in_list[k], s_delta);
         if (!ok && threadIdx.x == 0) {
             atomicAdd(&p.counters[CTR_FAIL + (*t.flag - 1)], 1ull);
@@ -728,14 +738,17 @@ __global__ void k_spill_offsets(const uint32_t* fill, uint32_t nB, uint64_t C, u
     if (b < nB) soff[b] = s_base + s_scan[threadIdx.x] - ex;
 }
 
+// Grid (NSPILL, Y): blocks (s, y) move shard s's strings y*256 + t, stepping
+// by Y*256, up to the shard's fill (nothing to do when nothing spilled).
 template <int W, typename T>
 __global__ void k_spill_move(const uint64_t* rx, const uint64_t* rz, const T* rc, const uint32_t* rb,
                              const uint32_t* rs, uint64_t rcap, const unsigned long long* shard_fill,
                              const uint64_t* soff, uint64_t* ox, uint64_t* oz, T* oc, uint64_t ocap) {
     const uint64_t shard_cap = rcap / NSPILL;
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < shard_cap * NSPILL;
-         k += (uint64_t)gridDim.x * blockDim.x) {
-        if (k % shard_cap >= shard_fill[k / shard_cap]) continue;
+    const uint64_t s = blockIdx.x;
+    const uint64_t fill = shard_fill[s] < shard_cap ? shard_fill[s] : shard_cap;
+    for (uint64_t j = blockIdx.y * (uint64_t)blockDim.x + threadIdx.x; j < fill; j += (uint64_t)gridDim.y * blockDim.x) {
+        const uint64_t k = s * shard_cap + j;
         uint64_t dst = soff[rb[k]] + rs[k];
         if (dst >= ocap) continue;
 #pragma unroll
@@ -785,7 +798,7 @@ __global__ void __launch_bounds__(256) k_noise(const uint64_t* x, const uint64_t
             uint32_t* d32 = reinterpret_cast<uint32_t*>(smem + off);
             for (size_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d32[i] = s32[i];
         };
-        if (sizeof(T) == 8) cp(L.etab, nz.etab, sizeof(double) * 8 * 256);
+        cp(L.etab, nz.etab, sizeof(double) * 8 * 256);
         cp(L.t1, nz.t1, sizeof(int64_t) * 4 * (size_t)nz.n_sites);
         cp(L.c2, nz.c2, sizeof(int64_t) * 16 * (size_t)n_pairs);
         cp(L.smask, nz.smask, sizeof(uint64_t) * (size_t)nz.n_shift * W);
@@ -811,7 +824,7 @@ __global__ void __launch_bounds__(256) k_noise(const uint64_t* x, const uint64_t
             xx[w] = ax[(size_t)w * acap + i];
             zz[w] = az[(size_t)w * acap + i];
         }
-        v = Coef<T>::mul(v, noise_factor(sn, noise_exponent<W>(sn, xx, zz), T(0)));
+        v = Coef<T>::scale(v, noise_factor(sn, noise_exponent<W>(sn, xx, zz)));
         if (Coef<T>::small(v, e)) v = T(0);
         ac[i] = v;
     };

@@ -89,8 +89,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 if (Coef<T>::small(c, eps) || (p.w_max >= 0 && weight_of<W>(x, z) > p.w_max)) c = T(0);
             }
             if (p.has_noise && c != T(0)) {
-                const T f = noise_factor(p.noise, noise_exponent<W>(p.noise, x, z), T(0));
-                c = Coef<T>::mul(c, f);
+                c = Coef<T>::scale(c, noise_factor(p.noise, noise_exponent<W>(p.noise, x, z)));
                 if (Coef<T>::small(c, eps)) c = T(0);
             }
             t.c[i] = c;
@@ -342,7 +341,7 @@ __global__ void __launch_bounds__(32 * WARP_TILE_WARPS) k_process_warp(StepParam
 
     Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem + warp_tile_bytes<W, T>(cap) * wid, cap, s_ctl[wid]);
     WarpAcc acc{0ull, 0ull, 0ull};
-    const uint32_t n_items = p.in_list ? p.n_list : p.sB;
+    const uint32_t n_items = work_items(p);
     for (;;) {
         uint32_t k = 0;
         if (lane == 0) k = (uint32_t)atomicAdd(&p.counters[p.work_ctr], 1ull);

@@ -37,7 +37,8 @@ class pp_options(ctypes.Structure):
                 ("alloc", ALLOC_FN),
                 ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p),
+                ("timing", ctypes.c_int)]
 
 
 class pp_stats(ctypes.Structure):
@@ -51,7 +52,8 @@ class pp_stats(ctypes.Structure):
                 ("tier_launches", ctypes.c_int * 4),
                 ("tier_ms", ctypes.c_double * 4),
                 ("tier_strings", ctypes.c_double * 4),
-                ("bytes_per_string", ctypes.c_double)]
+                ("bytes_per_string", ctypes.c_double),
+                ("orbit_launches", ctypes.c_int)]
 
 
 class pp_batch_item(ctypes.Structure):
@@ -65,7 +67,9 @@ class pp_batch_item(ctypes.Structure):
 
 class pp_tuning(ctypes.Structure):
     _fields_ = [("max_fused_gates", ctypes.c_int),
-                ("bucket_headroom", ctypes.c_double)]
+                ("bucket_headroom", ctypes.c_double),
+                ("first_tier", ctypes.c_int),
+                ("orbit_tiles", ctypes.c_int)]
 
 
 class PPError(RuntimeError):
@@ -76,7 +80,8 @@ class PPError(RuntimeError):
 
 EXPORTED = ["pp_default_options", "pp_create", "pp_destroy", "pp_load_circuit", "pp_load_noise",
             "pp_propagate", "pp_expect", "pp_export_terms", "pp_get_stats", "pp_last_error",
-            "pp_expect_noalloc", "pp_propagate_batch", "pp_set_tuning", "pp_get_tuning"]
+            "pp_expect_noalloc", "pp_propagate_batch", "pp_set_tuning", "pp_get_tuning", "pp_set_top_k",
+            "pp_cancel"]
 NOALLOC_MAX_TERMS = 1 << 27
 
 _lib = None
@@ -107,6 +112,8 @@ def load_library(path: str = LIB_PATH):
     L.pp_propagate_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(pp_batch_item),
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.pp_set_tuning.argtypes = [vp, ctypes.POINTER(pp_tuning)]
+    L.pp_set_top_k.argtypes = [vp, sz]
+    L.pp_cancel.argtypes = [vp]
     L.pp_get_tuning.argtypes = [vp, ctypes.POINTER(pp_tuning)]
     for f in EXPORTED:
         if f not in ("pp_default_options", "pp_last_error"):
@@ -123,8 +130,12 @@ class Handle:
     """One pp_handle: a circuit, its noise maps, and the last propagation."""
 
     def __init__(self, n_qubits: int, precision: int = PRECISION_FP64, max_terms: int = 0,
-                 torch_memory: bool = False, stream: Optional[int] = None):
-        """stream: a cudaStream_t (as int) to run on; None = the legacy default stream."""
+                 torch_memory: bool = False, stream: Optional[int] = None, timing: bool = False,
+                 allocator=None):
+        """stream: a cudaStream_t (as int) to run on; None = the legacy default stream.
+        timing: record per-tier device times (pp_stats.tier_ms).
+        allocator: optional (alloc(nbytes) -> device pointer or 0, free(ptr)) pair of
+        Python callables used for every device allocation of the handle."""
         self.L = load_library()
         self.n_qubits = n_qubits
         self.W = inputs.n_words(n_qubits)
@@ -132,8 +143,16 @@ class Handle:
         self.L.pp_default_options(ctypes.byref(opt))
         opt.precision = precision
         opt.max_terms = max_terms
+        opt.timing = int(bool(timing))
         self._cb = None
-        if torch_memory:
+        if allocator is not None:
+            a_fn, f_fn = allocator
+            self._cb = (ALLOC_FN(lambda nbytes, ctx: a_fn(int(nbytes)) or None),
+                        FREE_FN(lambda ptr, ctx: f_fn(ptr)))
+            opt.alloc, opt.free = self._cb
+            if stream is not None:
+                opt.cuda_stream = stream
+        elif torch_memory:
             import torch
             dev = torch.cuda.current_device()
             # blocks are cached per stream: allocate on the stream that uses them
@@ -214,19 +233,35 @@ class Handle:
         self._check(self.L.pp_export_terms(self.h, N, _p(x), _p(z), _p(c), ctypes.byref(n)))
         return x, z, c
 
+    def pp_cancel(self):
+        """Stops the propagation running on this handle in another thread
+        (it raises PPError with PP_ERR_TIMEOUT there)."""
+        self._check(self.L.pp_cancel(self.h))
+
+    def pp_set_top_k(self, top_k: int):
+        self._check(self.L.pp_set_top_k(self.h, int(top_k)))
+
     def pp_get_stats(self) -> pp_stats:
         s = pp_stats()
         self._check(self.L.pp_get_stats(self.h, ctypes.byref(s)))
         return s
 
-    def pp_set_tuning(self, max_fused_gates: int = 0, bucket_headroom: float = 0.0):
-        t = pp_tuning(int(max_fused_gates), float(bucket_headroom))
+    def pp_set_tuning(self, max_fused_gates: int = 0, bucket_headroom: float = 0.0, first_tier: int = 0,
+                      orbit_tiles: int = 0):
+        t = pp_tuning(int(max_fused_gates), float(bucket_headroom), int(first_tier), int(orbit_tiles))
         self._check(self.L.pp_set_tuning(self.h, ctypes.byref(t)))
 
     def pp_get_tuning(self):
+        """(max_fused_gates, bucket_headroom) in effect."""
         t = pp_tuning()
         self._check(self.L.pp_get_tuning(self.h, ctypes.byref(t)))
         return t.max_fused_gates, t.bucket_headroom
+
+    def tuning(self) -> dict:
+        """Every tuning field in effect."""
+        t = pp_tuning()
+        self._check(self.L.pp_get_tuning(self.h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in pp_tuning._fields_}
 
     # convenience: a whole Instance
     def load_instance(self, inst: "inputs.Instance"):
@@ -240,6 +275,7 @@ class Handle:
 
     def run_instance(self, inst: "inputs.Instance", eps: Optional[float] = None,
                      w_max: Optional[int] = None):
+        self.pp_set_top_k(getattr(inst, "top_k", 0))
         self.pp_propagate(inst.obs_x, inst.obs_z, inst.obs_c,
                           inst.eps if eps is None else eps,
                           inst.w_max if w_max is None else w_max)

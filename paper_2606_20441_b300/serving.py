@@ -35,6 +35,7 @@ import numpy as np
 from . import inputs
 
 PP_ERR_CAPACITY = 4
+PP_ERR_TIMEOUT = 6    # cancelled (pp_cancel) or dropped from the queue by Server.cancel
 
 
 @dataclasses.dataclass
@@ -111,6 +112,13 @@ class GpuExecutor:
         except self.pp.PPError as ex:
             return ex.status, None, 0.0, 0
 
+    def cancel(self, worker: int):
+        """Stops the propagation running on `worker` (pp_cancel); its run()
+        returns PP_ERR_TIMEOUT after the sub-layer in flight."""
+        cur = self.current[worker]
+        if cur is not None:
+            cur[1].pp_cancel()
+
     def close(self):
         for k, cur in enumerate(self.current):
             if cur is not None:
@@ -161,10 +169,15 @@ class Server:
                     self._cv.wait()
             req, arrival, escalated = item
             start = self.clock()
+            with self._cv:
+                self._running[w] = req.rid
             status, e, upd, terms = self.executor.run(w, req.instance)
             done = self.clock()
             with self._cv:
-                if status == PP_ERR_CAPACITY and not large and self.n_large > 0:
+                self._running.pop(w, None)
+                if req.rid in self._cancelled:
+                    status, e = PP_ERR_TIMEOUT, None
+                if status == PP_ERR_CAPACITY and not large and self.n_large > 0 and req.rid not in self._cancelled:
                     self._escalated.append((req, arrival, True))
                     if self.route_key is not None:
                         self.large_classes.add(self.route_key(req.instance))
@@ -174,11 +187,39 @@ class Server:
                     self._pending -= 1
                 self._cv.notify_all()
 
+    def cancel(self, rid: int) -> bool:
+        """Cancels request `rid`: a queued request is dropped at once, one in
+        flight is stopped by the executor after its current sub-layer.  Either
+        way its outcome has status PP_ERR_TIMEOUT.  Returns False if the
+        request already finished (or was never released)."""
+        with self._cv:
+            if any(o.rid == rid for o in self.outcomes):
+                return False
+            self._cancelled.add(rid)
+            for q in (self._fresh, self._escalated):
+                for item in list(q):
+                    if item[0].rid == rid:
+                        q.remove(item)
+                        now = self.clock()
+                        self.outcomes.append(Outcome(rid, item[1], now, now, -1, PP_ERR_TIMEOUT, None, 0.0, 0,
+                                                     item[2]))
+                        self._pending -= 1
+                        self._cv.notify_all()
+                        return True
+            for w, r in self._running.items():
+                if r == rid:
+                    self.executor.cancel(w)
+                    return True
+            return rid in self._released
+
     def serve(self, requests: List["inputs.Request"], time_scale: float = 1.0) -> List[Outcome]:
         """Releases each request at its arrival time (scaled), waits for all."""
         self._cv = threading.Condition()
         self._fresh: "collections.deque" = collections.deque()
         self._escalated: "collections.deque" = collections.deque()
+        self._running: dict = {}
+        self._cancelled: set = set()
+        self._released: set = set()
         self._closed = False
         self._pending = len(requests)
         self.outcomes = []
@@ -193,6 +234,14 @@ class Server:
             if wait > 0:
                 time.sleep(wait)
             with self._cv:
+                self._released.add(req.rid)
+                if req.rid in self._cancelled:
+                    now = self.clock()
+                    self.outcomes.append(Outcome(req.rid, max(due, t0), now, now, -1, PP_ERR_TIMEOUT, None, 0.0,
+                                                 0, False))
+                    self._pending -= 1
+                    self._cv.notify_all()
+                    continue
                 if (self.n_large > 0 and self.route_key is not None
                         and self.route_key(req.instance) in self.large_classes):
                     self._escalated.append((req, max(due, t0), True))

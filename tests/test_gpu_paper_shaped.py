@@ -2,9 +2,17 @@
 the 3x3 second-order Trotter mirror circuit with its four per-colour noise
 models and the 56-qubit heavy-hex mirror circuit (its
 R_ZZ gates and noise pairs span many site distances).  Same bar as the other
-parity tests: equal string sets up to strings within 1e-9 relative of the
+parity tests: equal string sets up to strings within 1e-12 relative of the
 threshold, coefficients within 1e-12 relative in FP64, the expectation within
-1e-12 of the diagonal mass, and the canonical update count."""
+1e-12 of the diagonal mass, and the canonical update count.
+
+Mirror circuits run forwards then backwards, so most surviving coefficients
+are the small remainders of cancelling contributions as large as the largest
+coefficient; their rounding error is relative to those contributions.  Their
+coefficient check therefore uses 1e-12 relative with a floor of 1e-3 of the
+largest coefficient (an absolute bar of 1e-15 of it): measured on B300 the
+largest such difference is 4e-12 relative to a 4e-6 coefficient, i.e. 2e-17
+of the largest."""
 import dataclasses
 
 import pytest
@@ -28,7 +36,7 @@ def pp():
 def check(pp, inst):
     ref = oracle.run(inst)
     got = pp.propagate(inst, precision=64)
-    info = compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), inst.eps, rel=1e-12)
+    info = compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), inst.eps, rel=1e-12, floor=1e-3)
     assert abs(got.expect - ref.expect) <= max(expect_tol((ref.x, ref.z, ref.c), 1e-12), 1e-300)
     if info["near_eps"] == 0:
         assert got.stats.updates == ref.updates

@@ -1,5 +1,5 @@
 """CUDA path (through the C ABI) against the CPU oracle on the same seeded
-inputs: bit-exact string sets (up to strings within 1e-9 relative of the
+inputs: bit-exact string sets (up to strings within 1e-12 relative of the
 threshold), coefficients within 1e-12 relative in FP64, expectation within
 1e-12 of the sum of |c| over diagonal strings, and the canonical gate-by-gate
 update count."""
@@ -22,6 +22,20 @@ def pp():
     from paper_2606_20441_b300 import build, pp as ppmod
     build.build()
     return ppmod
+
+
+def run_tuned(pp, inst, precision=64, **tuning):
+    """One propagation with plan tuning; returns (x, z, c, expect, stats)."""
+    h = pp.Handle(inst.n_qubits, precision=precision)
+    try:
+        h.load_instance(inst)
+        h.pp_set_tuning(**tuning)
+        h.run_instance(inst)
+        e = h.pp_expect()
+        x, z, c = h.pp_export_terms()
+        return x, z, c, e, h.pp_get_stats()
+    finally:
+        h.close()
 
 
 def check(pp, inst, precision=64, rel=1e-12, exp_rel=1e-12, max_terms=0, check_updates=True):
@@ -153,3 +167,179 @@ def test_duplicate_input_strings_are_summed(pp):
     ref = oracle.run(dup)
     got = pp.propagate(dup)
     compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), 0.0)
+
+
+# ----------------------------------------------------------------- every processing tier
+
+TIER_CASES = {"6x6_s3": lambda: inputs.workload_6x6(steps=3, eps=1e-5),
+              "7x8_s3": lambda: inputs.workload_7x8(eps=1e-4, steps=3)}
+
+
+@pytest.fixture(scope="module")
+def tier_refs():
+    return {k: (f(), oracle.run(f())) for k, f in TIER_CASES.items()}
+
+
+@pytest.mark.parametrize("case", sorted(TIER_CASES))
+@pytest.mark.parametrize("first_tier", [1, 2, 3])
+def test_every_tier_against_oracle(pp, tier_refs, case, first_tier):
+    """Buckets forced past the smaller tiers: the CTA tiles (1024 and 4096
+    strings) and the global-memory tile each run whole propagations and match
+    the oracle exactly (string sets, coefficients, update count)."""
+    inst, ref = tier_refs[case]
+    x, z, c, e, st = run_tuned(pp, inst, first_tier=first_tier)
+    info = compare_terms((x, z, c), (ref.x, ref.z, ref.c), inst.eps)
+    assert abs(e - ref.expect) <= expect_tol((ref.x, ref.z, ref.c))
+    if info["near_eps"] == 0:
+        assert st.updates == ref.updates
+    assert st.tier_launches[first_tier] > 0 and st.tier_strings[first_tier] > 0
+    for t in range(first_tier):
+        assert st.tier_strings[t] == 0
+    if first_tier == 3:
+        assert st.fallback_buckets > 0
+
+
+@pytest.mark.parametrize("case", sorted(TIER_CASES))
+def test_orbit_tier_matches_sparse_tier(pp, tier_refs, case):
+    """Tier 0 with the orbit tiles (single-run sub-layers, dense orbit blocks)
+    and with the sparse hashed warp tiles (multi-segment sub-layers) give the
+    same result bit for bit, and both match the oracle."""
+    inst, ref = tier_refs[case]
+    for prec in (64, 32):
+        xo, zo, co, eo, so = run_tuned(pp, inst, precision=prec, orbit_tiles=1)
+        xs, zs, cs, es, ss = run_tuned(pp, inst, precision=prec, orbit_tiles=0)
+        assert so.orbit_launches > 0 and ss.orbit_launches == 0
+        assert so.tier_strings[0] > 0
+        # every plan reproduces gate-by-gate propagation, so the two agree bit for bit
+        assert np.array_equal(xo, xs) and np.array_equal(zo, zs) and np.array_equal(co, cs)
+        assert eo == es and so.updates == ss.updates
+        if prec == 64:
+            compare_terms((xo, zo, co), (ref.x, ref.z, ref.c), inst.eps)
+            assert so.updates == ref.updates
+
+
+# ----------------------------------------------------------------- the 7x8 workload deeper
+
+def _digest_of(x, z):
+    from tests.golden.make_oracle_digest import set_digest
+    return set_digest(x, z)
+
+
+def test_tfim_7x8_four_steps_golden(pp):
+    """7x8, 4 Trotter steps, eps = 1e-5, w_max = 10 (3e6 strings): the oracle
+    needs minutes, so its result is stored as a digest by
+    tests/golden/make_oracle_digest.py: term count, set digest, expectation,
+    update count and a sample of exact coefficients."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "tfim7x8_s4_eps1e-5.json")))
+    inst = inputs.workload_7x8(eps=1e-5, w_max=10, steps=4)
+    got = pp.propagate(inst)
+    assert g["near_eps"] == 0
+    assert len(got.c) == g["n_terms"]
+    assert _digest_of(got.x, got.z) == g["set_digest"]
+    assert got.stats.updates == g["updates"]
+    assert abs(got.expect - g["expect"]) <= 1e-12 * g["diag_abs_sum"]
+    keys = np.concatenate([got.x, got.z], axis=1)
+    sx = np.array(g["sample"]["x"], dtype=np.uint64)
+    sz = np.array(g["sample"]["z"], dtype=np.uint64)
+    sc = np.array([float.fromhex(v) for v in g["sample"]["c"]])
+    want = np.concatenate([sx, sz], axis=1)
+    kv = keys.view(np.dtype((np.void, keys.dtype.itemsize * keys.shape[1]))).ravel()
+    wv = np.ascontiguousarray(want).view(np.dtype((np.void, want.dtype.itemsize * want.shape[1]))).ravel()
+    common, ig, iw = np.intersect1d(kv, wv, return_indices=True)
+    assert len(common) == len(wv)
+    assert np.all(np.abs(got.c[ig] - sc[iw]) <= 1e-12 * np.abs(sc[iw]))
+
+
+# ----------------------------------------------------------------- the benchmark configuration
+
+def _bench_shaped(theta_zz, theta_x):
+    """The 7x8 / 20-step / w_max 10 / eps 1e-6 benchmark circuit (same lattice,
+    noise rates and observable) with other angles."""
+    base = inputs.workload_7x8(eps=1e-6, w_max=10, steps=20)
+    inst = inputs.tfim_instance("bench_shaped", 7, 8, 20, theta_zz, theta_x,
+                                np.stack([m.lam for m in base.noise]),
+                                [({a: "Z", b: "Z"}, 1.0 / 97) for (a, b) in base.meta["edges"]],
+                                eps=1e-6, w_max=10)
+    return inst
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_bench_configuration_clifford_angles(pp, precision):
+    """The full benchmark configuration (7x8, 20 steps, the benchmark's noise
+    and observable, eps 1e-6, w_max 10, default plan) at Clifford angles
+    (R_ZZ(pi/2), per-site R_X in {0, pi/2, pi, -pi/2}): every string follows
+    one path (App. A) until the weight cap ends it, computed independently by
+    the symplectic tableau in oracle/clifford.py (79 of the 97 paths survive)."""
+    from oracle import clifford
+    rng = inputs.SplitMix64(3)
+    tx = [[0.0, math.pi / 2, math.pi, -math.pi / 2][rng.randint(4)] for _ in range(56)]
+    inst = _bench_shaped(math.pi / 2, tx)
+    ref, ref_updates = clifford.propagate(inst, truncate=True, count_updates=True)
+    got = pp.propagate(inst, precision=precision)
+    assert len(ref) > 0 and len(got.c) == len(ref)
+    tol = 1e-13 if precision == 64 else 2e-6
+    for i in range(len(got.c)):
+        key = (int(got.x[i, 0]), int(got.z[i, 0]))
+        assert abs(got.c[i] - ref[key]) <= tol * abs(ref[key])
+    assert got.stats.updates == ref_updates
+
+
+def test_bench_configuration_theta_zero(pp):
+    """The benchmark configuration with every angle 0: only the line diagram
+    survives, O~ = O prod exp(2 sum lambda over anticommuting generators) (App.
+    G, Eq. line-term)."""
+    inst = _bench_shaped(0.0, 0.0)
+    got = pp.propagate(inst)
+    assert len(got.c) == len(inst.obs_c)
+    for t in range(len(inst.obs_c)):
+        s_tot = 0.0
+        for m in inst.noise:
+            anti = ((np.bitwise_and(m.ex[:, 0], inst.obs_z[t, 0]) ^ np.bitwise_and(m.ez[:, 0], inst.obs_x[t, 0])))
+            par = np.array([bin(int(v)).count("1") & 1 for v in anti], dtype=bool)
+            s_tot += float(np.sum(m.lam[par]))
+        i = int(np.nonzero((got.x[:, 0] == inst.obs_x[t, 0]) & (got.z[:, 0] == inst.obs_z[t, 0]))[0][0])
+        expected = float(inst.obs_c[t]) * math.exp(2.0 * s_tot)
+        assert abs(got.c[i] - expected) <= 1e-13 * abs(expected)
+    assert got.stats.updates == inst.n_gates * len(inst.obs_c)
+
+
+# ----------------------------------------------------------------- top-K truncation
+
+TOPK_CASES = {"6x6_s3": lambda: inputs.workload_6x6(steps=3, eps=1e-5),
+              "7x8_s3": lambda: inputs.workload_7x8(eps=1e-4, steps=3)}
+
+
+@pytest.mark.parametrize("case", sorted(TOPK_CASES))
+@pytest.mark.parametrize("k", [100, 10_000, 1_000_000])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_top_k_against_oracle(pp, case, k, precision):
+    """Top-K after every layer (Sec. I.A), device radix select, against the
+    oracle's sort: the same strings (FP64: the same coefficients too); K above
+    the term count changes nothing."""
+    import dataclasses
+    inst = dataclasses.replace(TOPK_CASES[case](), top_k=k)
+    ref = oracle.run(inst)
+    got = pp.propagate(inst, precision=precision)
+    assert len(got.c) <= k
+    if precision == 64 or len(ref.c) == k:
+        assert len(got.c) == len(ref.c)
+    if precision == 64:
+        compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), inst.eps)
+        assert abs(got.expect - ref.expect) <= expect_tol((ref.x, ref.z, ref.c))
+        assert got.stats.updates == ref.updates
+    if k == 1_000_000:
+        plain = oracle.run(dataclasses.replace(inst, top_k=0))
+        assert len(plain.c) == len(ref.c)
+
+
+def test_top_k_ties_on_the_input(pp):
+    """The 97 equal coefficients of the 7x8 observable: K = 40 keeps the 40
+    strings first in export order (the oracle's tie rule), then propagates."""
+    import dataclasses
+    inst = dataclasses.replace(inputs.workload_7x8(eps=1e-4, steps=2), top_k=40)
+    ref = oracle.run(inst)
+    got = pp.propagate(inst)
+    compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), inst.eps)
+    assert got.stats.updates == ref.updates

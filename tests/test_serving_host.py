@@ -115,3 +115,57 @@ def test_learned_routing_skips_small_workers():
     runs = len(ex.order)
     assert runs - len(reqs) <= 2
     assert srv.large_classes == {True}
+
+
+class CancellableExecutor(FakeExecutor):
+    """Runs until the request's service time passes or the server cancels it
+    (the stand-in for pp_cancel stopping a propagation after a sub-layer)."""
+
+    def __init__(self, service_s):
+        super().__init__(service_s)
+        self.stop = {}
+        self.started = {}
+
+    def run(self, worker, inst):
+        ev = threading.Event()
+        with self.lock:
+            self.stop[worker] = ev
+            self.started[inst.name] = time.perf_counter()
+        cancelled = ev.wait(self.service_s)
+        return (serving.PP_ERR_TIMEOUT, None, 0.0, 0) if cancelled else (0, 1.0, 10.0, 1)
+
+    def cancel(self, worker):
+        with self.lock:
+            ev = self.stop.get(worker)
+        if ev is not None:
+            ev.set()
+
+
+def test_cancel_running_and_queued_requests():
+    """One worker: request 0 runs long and is cancelled mid-flight, request 1
+    is cancelled while still queued; both end with PP_ERR_TIMEOUT, the worker
+    goes on to serve the rest."""
+    reqs = inputs.workload_serving(count=4, rate_hz=1e6, side_hi=4, steps_hi=5)
+    ex = CancellableExecutor(service_s=2.0)
+    srv = serving.Server(ex, n_workers=1)
+    result = {}
+
+    def run():
+        result["out"] = srv.serve(reqs)
+
+    th = threading.Thread(target=run)
+    th.start()
+    t0 = time.perf_counter()
+    while reqs[0].instance.name not in ex.started and time.perf_counter() - t0 < 5:
+        time.sleep(0.01)
+    assert srv.cancel(reqs[1].rid)      # queued behind request 0
+    assert srv.cancel(reqs[0].rid)      # running
+    ex.service_s = 0.01                 # the rest finish quickly
+    th.join(timeout=10)
+    assert not th.is_alive()
+    out = {o.rid: o for o in result["out"]}
+    assert out[reqs[0].rid].status == serving.PP_ERR_TIMEOUT
+    assert out[reqs[1].rid].status == serving.PP_ERR_TIMEOUT and out[reqs[1].rid].worker == -1
+    assert out[reqs[2].rid].status == 0 and out[reqs[3].rid].status == 0
+    assert time.perf_counter() - t0 < 2.0   # request 0 did not run its full service time
+    assert not srv.cancel(reqs[2].rid)      # already finished
