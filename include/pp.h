@@ -142,12 +142,17 @@ pp_status pp_cancel(pp_handle* h);
 pp_status pp_set_top_k(pp_handle* h, size_t top_k);
 
 /* <0..0|O~|0..0> = sum of c over strings with no X or Y letter, of the last
- * successful pp_propagate.  Accumulated exactly in 128-bit fixed point (terms
- * below 2^-80 in magnitude are cut), so the value does not depend on term order.
- * Synchronises.  Errors: PP_ERR_STATE. */
+ * successful pp_propagate (Sec. I.C: the noise-canceling observable's value
+ * on the all-zero state).  Accumulated exactly in 128-bit fixed point (terms
+ * below 2^-80 in magnitude are cut) and rounded once to the nearest double, so
+ * the value does not depend on term order.  Diagonal coefficients must be
+ * finite with |c| < 2^32 and sum in magnitude to less than 2^46; a value
+ * outside that range makes the result NaN.  Synchronises.  Errors:
+ * PP_ERR_STATE. */
 pp_status pp_expect(pp_handle* h, double* value);
 
-/* Copies O~ to caller-owned host buffers, sorted by (x, then z) as unsigned
+/* Copies O~ (Sec. I: the noise-canceling observable, a weighted sum of
+ * Pauli strings) to caller-owned host buffers, sorted by (x, then z) as unsigned
  * integers (word W-1 most significant).  The sort runs on the device (a radix
  * sort of the result, which stays sorted in the handle); the host only copies.
  * x, z: [cap][W], c: [cap] (FP64 in both precisions).  *n_out = number of
@@ -195,6 +200,8 @@ typedef struct {
     double bytes_per_string;  /* bytes of one stored string (x, z words and coefficient) */
     int orbit_launches;       /* tier-0 launches that used the orbit tiles (the rest of
                                  tier 0 used the sparse warp tiles)                      */
+    int retries;              /* sub-layers run twice because their output outgrew the
+                                 planned buckets and the overflow area                   */
 } pp_stats;
 
 pp_status pp_get_stats(const pp_handle* h, pp_stats* out);
@@ -207,8 +214,9 @@ const char* pp_last_error(const pp_handle* h);
  * (Sec. I, Eq. evolve_gate, truncation after every gate); only the run time
  * does.
  *   max_fused_gates  commuting gates fused into one sub-layer (one pass over
- *                    the strings), 1..64*W; 0 = library default (32).  More
- *                    gates mean fewer passes but larger orbits per bucket.
+ *                    the strings), 1..64*W; 0 = library default (64*W: whole
+ *                    layers).  More gates mean fewer passes but larger orbits
+ *                    per bucket.
  *   bucket_headroom  buckets are sized so that a bucket's strings times the
  *                    sub-layer's observed growth, times this factor, fill one
  *                    warp tile; in [1, 16]; 0 = library default (2.4).  Larger
@@ -246,7 +254,9 @@ pp_status pp_get_tuning(const pp_handle* h, pp_tuning* t);
  * while a stream is captured into a CUDA graph, applications whose own memory
  * pool owns the device and forbids other allocations, latency-critical paths
  * that must not enter the CUDA allocator.  It computes the same exact
- * fixed-point sum as pp_expect, over terms in the caller's device buffers,
+ * fixed-point sum as pp_expect, rounded by the same routine (the same bits for
+ * the same terms; NaN for a diagonal coefficient that is not finite or has
+ * |c| >= 2^32), over terms in the caller's device buffers,
  * without a handle and without allocating: its scratch (one 128-bit partial
  * per 16384 terms, 128 KiB) is a fixed array in the library's device image,
  * present on every GPU that loads the library until the process exits.

@@ -44,7 +44,7 @@ def main(argv=None) -> int:
 
     from . import pp
     inst = _instance(a.workload, a.eps, a.steps, a.w_max)
-    h = pp.Handle(inst.n_qubits, precision=a.precision, max_terms=a.max_terms)
+    h = pp.Handle(inst.n_qubits, precision=a.precision, max_terms=a.max_terms, timing=True)
     h.load_instance(inst)
     h.pp_set_tuning(a.fused_gates, a.headroom, a.first_tier, int(a.orbit_tiles))
     for _ in range(a.repeat):

@@ -24,7 +24,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 Setting = Tuple[int, float]   # (max_fused_gates, bucket_headroom)
 
-CANDIDATES: List[Setting] = [(32, 2.4), (16, 1.6), (24, 2.0), (32, 1.6), (32, 3.2), (16, 2.4)]
+# (0, 0.0) is the library default (whole layers, headroom 2.4)
+CANDIDATES: List[Setting] = [(0, 0.0), (32, 2.4), (16, 1.6), (64, 1.8), (32, 1.6), (64, 3.2)]
 
 
 def class_key(inst) -> str:

@@ -107,7 +107,6 @@ struct pp_handle {
     uint32_t* fill[2] = {nullptr, nullptr};
     uint32_t fill_cap = 0;
     unsigned long long* counters = nullptr;
-    long long* delta = nullptr;
     uint32_t* pass_list[N_TIERS - 1] = {nullptr, nullptr, nullptr};   // buckets passed tier t -> t+1
     size_t spill_cap = 0;          // overflow strings per layout
     Arena spill_raw, spill_grp;
@@ -245,8 +244,9 @@ int sig_kind(const SubLayerDesc& d) {
 // 2^(acting gates) strings, so smaller sub-layers keep orbits small enough for
 // the one-warp tiles at the price of more passes over the strings.
 int max_fused_gates(const pp_handle* h) {
-    // default: the measured best on the 7x8 TFIM workload (with bucket headroom 2.4)
-    int m = h->tune.max_fused_gates > 0 ? h->tune.max_fused_gates : 32;
+    // default: whole layers (up to 64 gates per mask word), the measured best on
+    // the 7x8 TFIM workload (three passes per Trotter step instead of six)
+    int m = h->tune.max_fused_gates > 0 ? h->tune.max_fused_gates : 64 * h->W;
     if (const char* e = getenv("PP_MAX_FUSED_GATES")) m = atoi(e);
     return std::max(1, std::min(m, 64 * h->W));
 }
@@ -487,7 +487,6 @@ size_t term_bytes(const pp_handle* h) {
     return 2 * (size_t)h->W * 8 + (h->opt.precision == PP_PRECISION_FP32 ? 4 : 8);
 }
 
-int tile_cap(const pp_handle* h) { return h->W == 1 ? kTiers[0].cap1 : kTiers[0].cap2; }
 
 // Bytes of one global-tier slice of `cap` strings (int32 indices).
 size_t global_slice_bytes(const pp_handle* h, int cap) {
@@ -537,7 +536,6 @@ void release_work_memory(pp_handle* h) {
         rel(h->soff[s]);
     }
     rel(h->counters);
-    rel(h->delta);
     for (auto& l : h->pass_list) rel(l);
     rel(h->partial);
     rel(h->topk_state);
@@ -596,14 +594,13 @@ pp_status ensure_memory_once(pp_handle* h) {
         if (!h->fill[s] || !h->soff[s]) return fail(h, PP_ERR_NOMEM, "bucket counters allocation failed");
     }
     h->counters = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * CTR_COUNT));
-    h->delta = static_cast<long long*>(dev_alloc(h, sizeof(long long) * MAX_SITES));
     for (int k = 0; k < N_TIERS - 1; ++k)
         if (!(h->pass_list[k] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap))))
             return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * (4096 + 1)));
     h->topk_state = static_cast<TopKState*>(dev_alloc(h, sizeof(TopKState)));
     if (!h->topk_state) return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
-    if (!h->spill_b || !h->spill_s || !h->counters || !h->delta || !h->partial)
+    if (!h->spill_b || !h->spill_s || !h->counters || !h->partial)
         return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
     return ensure_global_tier(h);
 }
@@ -678,11 +675,13 @@ OrbCaps orbit_caps() {
     return k;
 }
 
+int tier_cap(const pp_handle* h, int tier);
+
 template <int W, typename T>
 cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orbit, uint32_t n_items,
                            int* launches) {
     ++*launches;
-    const int cap = W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2;
+    const int cap = tier < kGlobalTier ? tier_cap(h, tier) : kTiers[tier].cap1;
     switch (tier) {
         case 0: {
             if (orbit) {
@@ -718,7 +717,18 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orb
     }
 }
 
-int tier_cap(const pp_handle* h, int tier) { return h->W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2; }
+// Tile entries of a shared-memory tier; PP_TILE_CAPS="c0,c1,c2" overrides the
+// table for measurements.
+int tier_cap(const pp_handle* h, int tier) {
+    int c = h->W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2;
+    if (tier < kGlobalTier) {
+        if (const char* e = getenv("PP_TILE_CAPS")) {
+            int v[3] = {0, 0, 0};
+            if (sscanf(e, "%d,%d,%d", &v[0], &v[1], &v[2]) == 3 && v[tier] >= 64 && v[tier] <= 8192) c = v[tier];
+        }
+    }
+    return c;
+}
 
 cudaError_t dispatch_process(pp_handle* h, const StepParams& p, int tier, bool orbit, uint32_t n_items,
                              int* launches) {
@@ -1271,7 +1281,6 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     p.eps_f = eps_float_ceil(eps);
     p.w_max = w_max;
     p.counters = h->counters;
-    p.delta = h->delta;
     p.rpx = h->spill_raw.x;
     p.rpz = h->spill_raw.z;
     p.rpc = h->spill_raw.c;
@@ -1290,7 +1299,6 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
     uint32_t B = buckets_for(0, (double)n_terms);
     uint64_t C = h->cap / B;
     unsigned long long ctr[CTR_COUNT];
-    long long dl[MAX_SITES];
     CK(cudaMemsetAsync(h->fill[side], 0, sizeof(uint32_t) * B, h->st));
     CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
     CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
@@ -1322,13 +1330,19 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         const bool fin = d.final_ != 0;
         const int kind = h->sub_kind[s];
         double est = std::max(64.0, (double)N * growth_of(s) * 1.3);
-        const uint32_t nB = fin ? 1 : buckets_for(s + 1, est);
-        const uint64_t nC = fin ? h->cap : h->cap / nB;
+        uint32_t nB = fin ? 1 : buckets_for(s + 1, est);
+        uint64_t nC = fin ? h->cap : h->cap / nB;
+        // A sub-layer whose output outgrew the planned buckets and the overflow
+        // area runs once more with buckets sized from its true output count:
+        // its source layout is only read, and its noise map (applied in place)
+        // is not applied again.
+        float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
+        unsigned long long passed[N_TIERS] = {0, 0, 0, 0};   // buckets tier t handed to t+1
+        for (int attempt = 0;; ++attempt) {
         PP_RANGE_PUSH("pp sub-layer");
         if (!fin) CK(cudaMemsetAsync(h->fill[side ^ 1], 0, sizeof(uint32_t) * nB, h->st));
         CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
         CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
-        CK(cudaMemsetAsync(h->delta, 0, sizeof(long long) * MAX_SITES, h->st));
         p.sx = h->arena[side].x;
         p.sz = h->arena[side].z;
         p.sc = h->arena[side].c;
@@ -1351,7 +1365,7 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         // applied by a streaming pass over the layout first.
         p.has_noise = d.noise >= 0 && d.first;
         if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
-        if (d.noise >= 0 && !d.first)
+        if (d.noise >= 0 && !d.first && attempt == 0)
             CK(apply_noise(h, h->noise[d.noise], side, B, C, n_over_in, p.eps, p.eps_f, &launches));
         for (int tier = 0; tier < N_TIERS; ++tier) {
             p.in_list = tier == 0 ? nullptr : h->pass_list[tier - 1];
@@ -1373,34 +1387,36 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
         }
         if (!fin) CK(group_spill(h, side ^ 1, nB, nC, &launches));
         CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaMemcpyAsync(dl, h->delta, sizeof(dl), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         PP_RANGE_POP();
         if (h->cancel_gen.load() == gen) return fail(h, PP_ERR_TIMEOUT, "cancelled after sub-layer %d", s);
-        float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
         for (int tier = 0; tier < N_TIERS; ++tier) {
+            ms[tier] = 0.f;
             if (h->timing) CK(cudaEventElapsedTime(&ms[tier], h->tier_ev[tier][0], h->tier_ev[tier][1]));
             stats.tier_ms[tier] += ms[tier];
             stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];
         }
-        unsigned long long passed[N_TIERS] = {ctr[CTR_DEFER], ctr[CTR_DEFER + 1], ctr[CTR_DEFER + 2], 0};
+        for (int tier = 0; tier < kGlobalTier; ++tier) passed[tier] = ctr[CTR_DEFER + tier];
         stats.fallback_buckets += (int)passed[kGlobalTier - 1];
         if (ctr[CTR_ERR_FALLBACK])
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s,
                         h->fb_cap);
+        if (ctr[CTR_ERR_REGION] && !fin && attempt == 0 && ctr[CTR_OUT] <= h->cap) {
+            growth[kind] = std::max(0.05, (double)ctr[CTR_OUT] / std::max<double>(1.0, (double)N));
+            nB = buckets_for(s + 1, std::max(64.0, 1.3 * (double)ctr[CTR_OUT]));
+            nC = h->cap / nB;
+            stats.retries++;
+            continue;
+        }
+        break;
+        }
         if (ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap)
             return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
                         "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap,
                         h->spill_cap);
         const unsigned long long n_spill_out = fin ? 0ull : ctr[CTR_SPILL_TOTAL];
-        // canonical gate-by-gate count: live terms entering each gate in listed
-        // order, from the sparse tiers' per-gate births and deaths, plus the
-        // lifetimes the orbit tier summed itself
-        double live = (double)ctr[CTR_PROLOGUE];
-        for (int j = 0; j < d.n_gates; ++j) {
-            updates += live;
-            live += (double)dl[j];
-        }
+        // canonical gate-by-gate count (live terms entering each gate in listed
+        // order), summed by the kernels over string lifetimes
         updates += (double)ctr[CTR_UPDATES];
         size_t Nout = (size_t)ctr[CTR_OUT];
         peak = std::max(peak, Nout);
@@ -1421,10 +1437,14 @@ pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const u
                     "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"orbit\": %d, \"n_in\": %zu, \"n_out\": %zu, "
                     "\"buckets_in\": %u, \"buckets_out\": %u, \"passed\": [%llu, %llu, %llu], "
                     "\"spill\": %llu, \"ms\": [%.4f, %.4f, %.4f, %.4f], "
+                    "\"tier_strings\": [%llu, %llu, %llu, %llu], "
                     "\"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
                     "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu]}\n",
                     s, d.cls, d.n_gates, (int)use_orbit(s), N, Nout, B, nB, passed[0], passed[1], passed[2],
-                    n_spill_out, ms[0], ms[1], ms[2], ms[3], ctr[CTR_FAIL], ctr[CTR_FAIL + 1],
+                    n_spill_out, ms[0], ms[1], ms[2], ms[3],
+                    ctr[CTR_LOADED] + ctr[CTR_EMITTED], ctr[CTR_LOADED + 1] + ctr[CTR_EMITTED + 1],
+                    ctr[CTR_LOADED + 2] + ctr[CTR_EMITTED + 2], ctr[CTR_LOADED + 3] + ctr[CTR_EMITTED + 3],
+                    ctr[CTR_FAIL], ctr[CTR_FAIL + 1],
                     ctr[CTR_FAIL + 2], ctr[CTR_PHASE], ctr[CTR_PHASE + 1], ctr[CTR_PHASE + 2], ctr[CTR_PHASE + 3],
                     ctr[CTR_PHASE_CTA], ctr[CTR_PHASE_CTA + 1], ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3]);
         if (N > 0) growth[kind] = std::max(0.05, (double)Nout / (double)N);
@@ -1468,11 +1488,7 @@ pp_status pp_expect(pp_handle* h, double* value) {
     CK(cudaMemcpyAsync(&tot, h->partial + grid, sizeof(__int128), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     // the exact fixed-point total (units of 2^-80), rounded once to double
-    bool neg = tot < 0;
-    unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
-    long double v = (long double)(uint64_t)(mag >> 64) * 18446744073709551616.0L + (long double)(uint64_t)mag;
-    v = std::ldexp(v, -80);
-    *value = (double)(neg ? -v : v);
+    *value = fixed80_to_double(tot);
     return PP_OK;
 }
 

@@ -110,6 +110,24 @@ struct NoiseDesc {
 
 __device__ __forceinline__ int popc64(uint64_t v) { return __popcll(v); }
 
+// Leading zeros of a nonzero word, and a double from its bits, on host and device.
+__host__ __device__ inline int clz64_hd(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return __builtin_clzll(v);
+#endif
+}
+__host__ __device__ inline double __longlong_as_double_hd(long long b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double d;
+    __builtin_memcpy(&d, &b, sizeof(d));
+    return d;
+#endif
+}
+
 template <int W>
 __device__ __forceinline__ void shr_words(const uint64_t* v, int d, uint64_t* out) {
     // out = v >> d as a W-word little-endian integer (0 <= d < 64*W)
@@ -464,6 +482,16 @@ template <> struct Coef<float> {
     }
 };
 
+// The exact expectation sum: every diagonal coefficient becomes trunc(v * 2^80)
+// as a 128-bit integer and the integers are added.  Coefficients must be finite
+// with |v| < 2^32 (FIX80_LIMIT); a partial sum that met any other value is the
+// sentinel FIX80_INVALID, and the result is then NaN.  With the sum of |v|
+// below 2^46 no partial sum can reach the sentinel or wrap around.
+constexpr double FIX80_LIMIT = 4294967296.0;
+#define FIX80_INVALID ((__int128)(((unsigned __int128)1) << 127))
+
+__host__ __device__ inline bool fix80_valid(double v) { return v > -FIX80_LIMIT && v < FIX80_LIMIT; }
+
 // trunc(v * 2^80) as a 128-bit two's-complement integer (|v| < 2^46).
 __device__ __forceinline__ __int128 to_fixed80(double v) {
     uint64_t bits = (uint64_t)__double_as_longlong(v);
@@ -476,6 +504,39 @@ __device__ __forceinline__ __int128 to_fixed80(double v) {
     else if (sh < 0) mag = (__int128)(m >> (-sh));
     else mag = ((__int128)m) << sh;
     return (bits >> 63) ? -mag : mag;
+}
+
+// A 128-bit fixed-point total (units of 2^-80) rounded once to the nearest
+// double (ties to even), in integer arithmetic; FIX80_INVALID gives NaN.  The
+// host and the device use this one routine, so pp_expect and
+// pp_expect_noalloc return the same bits.
+__host__ __device__ inline double fixed80_to_double(__int128 tot) {
+    if (tot == FIX80_INVALID) return __longlong_as_double_hd(0x7ff8000000000000LL);
+    const bool neg = tot < 0;
+    const unsigned __int128 mag = neg ? (unsigned __int128)0 - (unsigned __int128)tot : (unsigned __int128)tot;
+    if (mag == 0) return 0.0;
+    const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
+    const int top = hi ? 127 - clz64_hd(hi) : 63 - clz64_hd(lo);   // highest set bit
+    uint64_t m;
+    int e = 0;   // the value is m * 2^(e - 80), m < 2^53
+    if (top <= 52) {
+        m = lo;
+    } else {
+        e = top - 52;
+        m = (uint64_t)(mag >> e);
+        const unsigned __int128 rem = mag & ((((unsigned __int128)1) << e) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (e - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            ++m;
+            if (m == (1ull << 53)) {
+                m >>= 1;
+                ++e;
+            }
+        }
+    }
+    // m < 2^53 is exact in a double; scaling by a power of two is exact
+    const double v = ldexp((double)m, e - 80);
+    return neg ? -v : v;
 }
 
 }  // namespace pp

@@ -51,7 +51,6 @@ struct StepParams {
     int w_max;
 
     unsigned long long* counters; // see CTR_* below
-    long long* delta;             // [MAX_SITES] net change of live terms by listed gate
     const uint32_t* in_list;      // buckets to process (nullptr: all of 0..sB-1)
     uint32_t n_list;
     const unsigned long long* n_list_dev;   // when set, in_list's length is read here (the
@@ -67,7 +66,7 @@ struct StepParams {
 enum {
     CTR_WORK = 0,        // work queues, one per tier (0..3)
     CTR_OUT = 4,         // terms written (next layout or final)
-    CTR_PROLOGUE = 5,    // live terms after the prologue (merge / noise)
+    CTR_PROLOGUE = 5,    // (unused)
     CTR_DEFER = 6,       // buckets passed from tier t to tier t+1 (6..8)
     CTR_ERR_REGION = 9,  // strings dropped: overflow area or result full
     CTR_ERR_FALLBACK = 10, // buckets too large even for the global tier
@@ -78,7 +77,7 @@ enum {
     CTR_SPILL_TOTAL = 24,// scratch of the overflow grouping
     CTR_PHASE = 28,      // tier-0 cycles per phase when tracing (28..31)
     CTR_PHASE_CTA = 32,  // CTA-tier cycles per phase when tracing (32..35)
-    CTR_UPDATES = 36,    // canonical work count of the buckets the orbit tier completed
+    CTR_UPDATES = 36,    // canonical work count of the completed buckets (string lifetimes)
     CTR_COUNT = 37
 };
 
@@ -180,6 +179,36 @@ __device__ __forceinline__ int tile_lookup(const Tile<W, T, I>& t, const uint64_
     return -1;
 }
 
+// tile_lookup that also reports, for an absent key, the first empty slot on
+// its probe path (where tile_insert_at starts).
+template <int W, typename T, typename I>
+__device__ __forceinline__ int tile_lookup_at(const Tile<W, T, I>& t, const uint64_t* x, const uint64_t* z,
+                                              uint32_t* slot) {
+    uint32_t h = tile_hash<W>(x, z, t.hbits);
+    for (int probe = 0; probe < t.hcap; ++probe) {
+        int s = (int)t.hash[h];
+        if (s < 0) {
+            *slot = h;
+            return -1;
+        }
+        if (tile_key_eq<W, T, I>(t, s, x, z)) return s;
+        h = (h + 1) & (uint32_t)(t.hcap - 1);
+    }
+    *slot = h;
+    return -1;
+}
+
+// Inserts entry idx (no key of the table equals its key) probing from slot h
+// on its probe path: slots taken meanwhile are skipped.
+template <int W, typename T, typename I>
+__device__ __forceinline__ void tile_insert_at(const Tile<W, T, I>& t, int idx, uint32_t h) {
+    for (int probe = 0; probe < t.hcap; ++probe) {
+        if ((int)atomic_cas_idx(&t.hash[h], (I)-1, (I)idx) < 0) return;
+        h = (h + 1) & (uint32_t)(t.hcap - 1);
+    }
+    atomicExch(t.flag, (int)FAIL_HASH);
+}
+
 // Inserts entry idx (key and coefficient already stored).  merge: if the key is
 // present, add the coefficient into the existing entry and leave idx dead.
 template <int W, typename T, typename I>
@@ -268,7 +297,7 @@ __device__ __forceinline__ void emit(const StepParams& p, uint32_t nb, const uin
 // This serves the buckets too large for one warp (see k_process_warp).
 template <int W, typename T, typename I>
 __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab, const ActDesc& ad,
-                               const ActDesc& adn, const StepParams& p, uint32_t b, int* s_delta) {
+                               const ActDesc& adn, const StepParams& p, uint32_t b) {
     const SubLayerDesc& d = *p.desc;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31;
@@ -284,7 +313,9 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
     };
 
     for (int i = tid; i < t.hcap; i += nt) t.hash[i] = (I)-1;
-    for (int i = tid; i < MAX_SITES; i += nt) s_delta[i] = 0;
+    // work count per lifetime (see pp_warp.cuh): births subtract g + 1, deaths
+    // add g + 1, strings alive at the end add the sub-layer's gate count
+    long long upd = 0;
     if (tid == 0) {
         *t.n = (int)n_in;
         *t.flag = (n_in > p.max_load) ? (int)FAIL_LOAD : 0;
@@ -390,6 +421,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
             const int k = k0 + tid;
             bool create = false, revive = false;
             int j = -1, gg = -1;
+            uint32_t hslot = 0;
             T v = T(0);
             uint64_t qx[W], qz[W], gm[W];
             if (k < na) {
@@ -411,7 +443,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                     qz[w] = z[w] ^ tab.rz[gg][w];
                 }
                 t.gi[i] = (uint8_t)gg;
-                j = tile_lookup<W, T, I>(t, qx, qz);
+                j = tile_lookup_at<W, T, I>(t, qx, qz, &hslot);
                 // i R P = i^{1+e} (R xor P): sign of P's sin-branch into its partner
                 const int e = product_phase<W>(tab.rx[gg], tab.rz[gg], x, z);
                 const int phi = ((1 + e) & 3) == 0 ? 1 : -1;
@@ -468,17 +500,10 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                 }
                 if (create) {
                     __threadfence_block();
-                    tile_insert<W, T, I>(t, idx, qx, qz, false);
+                    tile_insert_at<W, T, I>(t, idx, hslot);
                 }
                 join = more;
-            }
-            // per-gate count of strings born this round: lanes of equal gate add once
-            {
-                const unsigned bm = __ballot_sync(FULL, born);
-                if (bm) {
-                    const unsigned same = __match_any_sync(FULL, born ? gg : -1);
-                    if (born && lane == __ffs(same) - 1) atomicAdd(&s_delta[gg], __popc(same));
-                }
+                upd -= gg + 1;
             }
             act_append<W, T, I>(t, nxt, join, idx);
         }
@@ -486,26 +511,20 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
         if (*t.flag) return false;
         for (int k0 = 0; k0 < na; k0 += nt) {
             const int k = k0 + tid;
-            bool keep = false, dropped = false;
-            int i = 0, gd = -1;
+            bool keep = false;
+            int i = 0;
             if (k < na) {
                 i = (int)L[k];
                 T v = t.cn[i];
                 if (Coef<T>::small(v, eps)) {
                     v = T(0);
-                    dropped = true;
-                    gd = t.gi[i];
+                    upd += (int)t.gi[i] + 1;
                 }
                 t.c[i] = v;
                 if (v != T(0)) {
 #pragma unroll
                     for (int w = 0; w < W; ++w) keep |= t.g[(size_t)w * t.cap + i] != 0ull;
                 }
-            }
-            const unsigned dm = __ballot_sync(FULL, dropped);
-            if (dm) {
-                const unsigned same = __match_any_sync(FULL, gd);
-                if (dropped && lane == __ffs(same) - 1) atomicAdd(&s_delta[gd], -__popc(same));
             }
             act_append<W, T, I>(t, nxt, keep, i);
         }
@@ -523,6 +542,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
         int cnt = 0;
         for (int i = tid; i < nf; i += nt)
             if (t.c[i] != T(0)) ++cnt;
+        upd += (long long)cnt * d.n_gates;
         int off = cnt ? atomicAdd(t.live, cnt) : 0;
         __syncthreads();
         if (tid == 0) {
@@ -563,17 +583,15 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
             atomicAdd(&p.counters[CTR_OUT], (unsigned long long)cnt);
             atomicAdd(&p.counters[CTR_EMITTED + (p.work_ctr - CTR_WORK)], (unsigned long long)cnt);
         }
+        upd += (long long)cnt * d.n_gates;
     }
     __syncthreads();
     phase_mark(3);
-    if (tid == 0) {
-        atomicAdd(&p.counters[CTR_PROLOGUE], (unsigned long long)live0);
-        atomicAdd(&p.counters[CTR_LOADED + (p.work_ctr - CTR_WORK)], (unsigned long long)n_in);
-    }
-    for (int i = tid; i < MAX_SITES; i += nt)
-        if (s_delta[i])
-            atomicAdd(reinterpret_cast<unsigned long long*>(&p.delta[i]),
-                      (unsigned long long)(long long)s_delta[i]);   // two's complement
+    (void)live0;
+    if (tid == 0) atomicAdd(&p.counters[CTR_LOADED + (p.work_ctr - CTR_WORK)], (unsigned long long)n_in);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) upd += __shfl_xor_sync(FULL, upd, o);
+    if (lane == 0 && upd) atomicAdd(&p.counters[CTR_UPDATES], (unsigned long long)upd);
     return true;
 }
 
@@ -636,7 +654,6 @@ template <int W, typename T, int NT>
 __global__ void __launch_bounds__(NT) k_process(StepParams p, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int ctl[8];
-    __shared__ int s_delta[MAX_SITES];
     __shared__ uint32_t s_b;
     __shared__ GateTab<W, T> tab;
     __shared__ ActDesc s_ad, s_adn;
@@ -652,7 +669,7 @@ __global__ void __launch_bounds__(NT) k_process(StepParams p, int cap) {
         if (k >= n_items) break;
         const uint32_t b = p.in_list ? p.in_list[k] : k;
         if (p.sfill[b] != 0) {
-            bool ok = process_bucket<W, T, int16_t>(t, tab, s_ad, s_adn, p, b, s_delta);
+            bool ok = process_bucket<W, T, int16_t>(t, tab, s_ad, s_adn, p, b);
             if (!ok && threadIdx.x == 0) {
                 atomicAdd(&p.counters[CTR_FAIL + (*t.flag - 1)], 1ull);
                 if (p.out_list) {
@@ -673,7 +690,6 @@ template <int W, typename T>
 __global__ void __launch_bounds__(NWARPS * 32) k_process_global(StepParams p, unsigned char* scratch,
                                                                 size_t slice_bytes, int cap) {
     __shared__ int ctl[8];
-    __shared__ int s_delta[MAX_SITES];
     __shared__ uint32_t s_k;
     __shared__ GateTab<W, T> tab;
     __shared__ ActDesc s_ad, s_adn;
@@ -687,7 +703,7 @@ __global__ void __launch_bounds__(NWARPS * 32) k_process_global(StepParams p, un
         __syncthreads();
         const uint32_t k = s_k;
         if (k >= n_items) break;
-        bool ok = process_bucket<W, T, int32_t>(t, tab, s_ad, s_adn, p, p.in_list[k], s_delta);
+        bool ok = process_bucket<W, T, int32_t>(t, tab, s_ad, s_adn, p, p.in_list[k]);
         if (!ok && threadIdx.x == 0) {
             atomicAdd(&p.counters[CTR_FAIL + (*t.flag - 1)], 1ull);
             atomicAdd(&p.counters[CTR_ERR_FALLBACK], 1ull);
@@ -849,20 +865,25 @@ __global__ void k_expect(const uint64_t* x, const T* c, uint64_t cap, uint64_t n
                          __int128* partial) {
     __shared__ __int128 s[256];
     __int128 acc = 0;
+    bool bad = false;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         bool diag = true;
 #pragma unroll
         for (int w = 0; w < W; ++w) diag = diag && x[(size_t)w * cap + i] == 0ull;
-        if (diag) acc += to_fixed80((double)c[i]);
+        if (diag) {
+            const double v = (double)c[i];
+            if (fix80_valid(v)) acc += to_fixed80(v);
+            else bad = true;
+        }
     }
     s[threadIdx.x] = acc;
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
+    if (threadIdx.x == 0) partial[blockIdx.x] = bad ? FIX80_INVALID : s[0];
 }
 
 }  // namespace pp

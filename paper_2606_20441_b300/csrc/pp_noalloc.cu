@@ -41,39 +41,42 @@ __global__ void k_expect_noalloc_partials(const uint64_t* x, const double* c, si
     const size_t begin = (size_t)blockIdx.x * kNoAllocChunk;
     const size_t end = begin + kNoAllocChunk < n ? begin + kNoAllocChunk : n;
     __int128 acc = 0;
+    bool bad = false;
     for (size_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
         bool diag = true;
 #pragma unroll
         for (int w = 0; w < W; ++w) diag = diag && x[i * W + w] == 0ull;
-        if (diag) acc += pp::to_fixed80(c[i]);
+        if (diag) {
+            if (pp::fix80_valid(c[i])) acc += pp::to_fixed80(c[i]);
+            else bad = true;
+        }
     }
     s[threadIdx.x] = acc;
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+    if (threadIdx.x == 0) part[blockIdx.x] = bad ? FIX80_INVALID : s[0];
 }
 
 // One block folds the partials and writes the value as a double.
 __global__ void k_expect_noalloc_final(const __int128* part, int nparts, double* out) {
     __shared__ __int128 s[256];
     __int128 acc = 0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+    bool bad = false;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        if (part[i] == FIX80_INVALID) bad = true;
+        else acc += part[i];
+    }
     s[threadIdx.x] = acc;
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const __int128 tot = s[0];
-        const bool neg = tot < 0;
-        const unsigned __int128 mag = neg ? (unsigned __int128)(-tot) : (unsigned __int128)tot;
-        const double v = ((double)(uint64_t)(mag >> 64) * 18446744073709551616.0 + (double)(uint64_t)mag) * 0x1p-80;
-        *out = neg ? -v : v;
-    }
+    // rounded exactly as pp_expect rounds its total (same routine)
+    if (threadIdx.x == 0) *out = pp::fixed80_to_double(bad ? FIX80_INVALID : s[0]);
 }
 
 // Device address of the scratch array, looked up once per device.

@@ -29,14 +29,19 @@ static_assert(SORT_WARPS <= 32, "the warp offsets of a block scan fit one warp")
 __global__ void k_expect_final(__int128* partial, int n) {
     __shared__ __int128 s[256];
     __int128 acc = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const __int128 v = partial[i];
+        if (v == FIX80_INVALID) bad = true;
+        else acc += v;
+    }
     s[threadIdx.x] = acc;
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[n] = s[0];
+    if (threadIdx.x == 0) partial[n] = bad ? FIX80_INVALID : s[0];
 }
 
 // Key word kw in significance order: z[0..W-1], then x[0..W-1].

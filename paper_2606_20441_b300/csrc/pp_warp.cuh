@@ -26,9 +26,17 @@ struct WarpAcc {
     unsigned long long prologue, loaded, emitted;
 };
 
+// Work count (the canonical gate-by-gate number of live strings entering each
+// gate), kept per lifetime: a string live from listed gate b through listed
+// gate d (inclusive) contributes d - b + 1.  A lane adds g + 1 when a string
+// dies at gate g, subtracts g + 1 when one is born (created or revived) at
+// gate g, and adds the sub-layer's gate count for every string alive at the
+// end; strings of the input count from gate 0.
+
 template <int W, typename T>
 __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& tab, const ActDesc& ad,
-                            const ActDesc& adn, const StepParams& p, uint32_t b, int* wdelta, WarpAcc& acc) {
+                            const ActDesc& adn, const StepParams& p, uint32_t b, WarpAcc& acc,
+                            unsigned long long& upd_total) {
     const SubLayerDesc& d = *p.desc;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -48,8 +56,8 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         }
     };
     for (int i = lane; i < t.hcap; i += 32) t.hash[i] = (int16_t)-1;
-    for (int i = lane; i < 64 * W; i += 32) wdelta[i] = 0;
     if (lane == 0) *t.flag = 0;
+    long long upd = 0;   // this lane's share of the bucket's work count
     __syncwarp();
 
     // ---- load: the bucket's region, then its overflow strings
@@ -141,6 +149,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
             const int k = k0 + lane;
             bool create = false, revive = false;
             int i = 0, j = -1, gg = 0;
+            uint32_t hslot = 0;
             T v = T(0);
             uint64_t qx[W], qz[W], gm[W];
             if (k < na) {
@@ -163,7 +172,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                     qz[w] = z[w] ^ tab.rz[gg][w];
                 }
                 t.gi[i] = (uint8_t)gg;
-                j = tile_lookup<W, T, int16_t>(t, qx, qz);
+                j = tile_lookup_at<W, T, int16_t>(t, qx, qz, &hslot);
                 // i R P = i^{1+e} (R xor P): sign of P's sin-branch into its partner
                 const int e = product_phase<W>(tab.rx[gg], tab.rz[gg], x, z);
                 const int phi = ((1 + e) & 3) == 0 ? 1 : -1;
@@ -202,14 +211,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 }
             }
             bool join = false;
-            {
-                const bool born = create || revive;
-                if (__ballot_sync(FULL, born)) {
-                    const unsigned same = __match_any_sync(FULL, born ? gg : -1);
-                    if (born && lane == __ffs(same) - 1) wdelta[gg] += __popc(same);
-                }
-                __syncwarp();
-            }
+            if (create || revive) upd -= gg + 1;
             if (create || revive) {
                 // a new string, or one truncated earlier revived: it joins the
                 // orbit with the gates the orbit has left
@@ -222,7 +224,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 }
                 if (create) {
                     __threadfence_block();
-                    tile_insert<W, T, int16_t>(t, idx, qx, qz, false);
+                    tile_insert_at<W, T, int16_t>(t, idx, hslot);
                 }
                 join = more;
             }
@@ -239,26 +241,20 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         __syncwarp();
         for (int k0 = 0; k0 < na; k0 += 32) {
             const int k = k0 + lane;
-            bool keep = false, dropped = false;
-            int i = 0, gd = -1;
+            bool keep = false;
+            int i = 0;
             if (k < na) {
                 i = (int)L[k];
                 T v = t.cn[i];
                 if (Coef<T>::small(v, eps)) {
                     v = T(0);
-                    dropped = true;
-                    gd = t.gi[i];
+                    upd += (int)t.gi[i] + 1;
                 }
                 t.c[i] = v;
                 if (v != T(0)) {
 #pragma unroll
                     for (int w = 0; w < W; ++w) keep |= t.g[(size_t)w * t.cap + i] != 0ull;
                 }
-            }
-            if (__ballot_sync(FULL, dropped)) {
-                const unsigned same = __match_any_sync(FULL, gd);
-                if (dropped && lane == __ffs(same) - 1) wdelta[gd] -= __popc(same);
-                __syncwarp();
             }
             const unsigned km = __ballot_sync(FULL, keep);
             if (keep) Ln[nn + __popc(km & lt)] = (int16_t)i;
@@ -275,6 +271,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
     if (d.final_) {
         int cnt = 0;
         for (int i = lane; i < n; i += 32) cnt += t.c[i] != T(0);
+        upd += (long long)cnt * d.n_gates;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
         unsigned long long pos = 0;
@@ -311,14 +308,18 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
             tile_key<W, T, int16_t>(t, i, x, z);
             emit<W, T>(p, bucket_of<W>(adn, x, z, bmask), x, z, c);
         }
+        upd += (long long)cnt * d.n_gates;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
         emitted = (unsigned long long)cnt;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) upd += __shfl_xor_sync(FULL, upd, o);
     phase_mark(3);
     acc.prologue += (unsigned long long)live;
     acc.loaded += (unsigned long long)n_in;
     acc.emitted += emitted;
+    upd_total += (unsigned long long)upd;
     return true;
 }
 
@@ -326,13 +327,10 @@ template <int W, typename T>
 __global__ void __launch_bounds__(32 * WARP_TILE_WARPS) k_process_warp(StepParams p, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ GateTab<W, T> tab;
-    __shared__ int s_delta[MAX_SITES];
-    __shared__ int s_wdelta[WARP_TILE_WARPS][64 * W];   // per-bucket counts by listed gate
     __shared__ int s_ctl[WARP_TILE_WARPS][8];
     __shared__ unsigned long long s_acc[3];
     __shared__ ActDesc s_ad, s_adn;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < MAX_SITES; i += blockDim.x) s_delta[i] = 0;
     if (threadIdx.x < 3) s_acc[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
     if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
@@ -341,6 +339,7 @@ __global__ void __launch_bounds__(32 * WARP_TILE_WARPS) k_process_warp(StepParam
 
     Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem + warp_tile_bytes<W, T>(cap) * wid, cap, s_ctl[wid]);
     WarpAcc acc{0ull, 0ull, 0ull};
+    unsigned long long upd = 0;
     const uint32_t n_items = work_items(p);
     for (;;) {
         uint32_t k = 0;
@@ -349,10 +348,7 @@ __global__ void __launch_bounds__(32 * WARP_TILE_WARPS) k_process_warp(StepParam
         if (k >= n_items) break;
         const uint32_t b = p.in_list ? p.in_list[k] : k;
         if (p.sfill[b] == 0) continue;
-        if (warp_bucket<W, T>(t, tab, s_ad, s_adn, p, b, s_wdelta[wid], acc)) {
-            for (int i = lane; i < 64 * W; i += 32)
-                if (s_wdelta[wid][i]) atomicAdd(&s_delta[i], s_wdelta[wid][i]);
-        } else if (lane == 0) {
+        if (!warp_bucket<W, T>(t, tab, s_ad, s_adn, p, b, acc, upd) && lane == 0) {
             atomicAdd(&p.counters[CTR_FAIL + (*t.flag - 1)], 1ull);
             unsigned long long j = atomicAdd(&p.counters[p.defer_ctr], 1ull);
             p.out_list[j] = b;
@@ -360,18 +356,14 @@ __global__ void __launch_bounds__(32 * WARP_TILE_WARPS) k_process_warp(StepParam
         __syncwarp();
     }
     if (lane == 0) {
-        atomicAdd(&s_acc[0], acc.prologue);
+        atomicAdd(&s_acc[0], upd);
         atomicAdd(&s_acc[1], acc.loaded);
         atomicAdd(&s_acc[2], acc.emitted);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < MAX_SITES; i += blockDim.x)
-        if (s_delta[i])
-            atomicAdd(reinterpret_cast<unsigned long long*>(&p.delta[i]),
-                      (unsigned long long)(long long)s_delta[i]);   // two's complement
     if (threadIdx.x == 0) {
         const int tier = p.work_ctr - CTR_WORK;
-        if (s_acc[0]) atomicAdd(&p.counters[CTR_PROLOGUE], s_acc[0]);
+        if (s_acc[0]) atomicAdd(&p.counters[CTR_UPDATES], s_acc[0]);
         if (s_acc[1]) atomicAdd(&p.counters[CTR_LOADED + tier], s_acc[1]);
         if (s_acc[2]) {
             atomicAdd(&p.counters[CTR_EMITTED + tier], s_acc[2]);

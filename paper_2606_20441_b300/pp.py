@@ -53,7 +53,8 @@ class pp_stats(ctypes.Structure):
                 ("tier_ms", ctypes.c_double * 4),
                 ("tier_strings", ctypes.c_double * 4),
                 ("bytes_per_string", ctypes.c_double),
-                ("orbit_launches", ctypes.c_int)]
+                ("orbit_launches", ctypes.c_int),
+                ("retries", ctypes.c_int)]
 
 
 class pp_batch_item(ctypes.Structure):

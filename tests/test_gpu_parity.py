@@ -343,3 +343,23 @@ def test_top_k_ties_on_the_input(pp):
     got = pp.propagate(inst)
     compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), inst.eps)
     assert got.stats.updates == ref.updates
+
+
+def test_expectation_is_the_correctly_rounded_exact_sum(pp):
+    """<0|O~|0> is the exact sum of the diagonal coefficients rounded once
+    (App. C's estimator is a plain sum; the library sums in 128-bit fixed
+    point): 1 + 2^-53 + 2^-80 rounds to 1 + 2^-52, where adding in double
+    precision would give 1."""
+    from fractions import Fraction
+    terms = [({0: "Z"}, 1.0), ({1: "Z"}, 2.0 ** -53), ({2: "Z"}, 2.0 ** -80), ({0: "X"}, 0.75)]
+    ox, oz, oc = [], [], []
+    for letters, c in terms:
+        x, z = inputs.pauli_from_letters(letters, 1)
+        ox.append(x); oz.append(z); oc.append(c)
+    inst = inputs.Instance("exact", 3, np.zeros((0, 1), np.uint64), np.zeros((0, 1), np.uint64), np.zeros(0),
+                           np.zeros(0, np.int32), 1, [], np.array(ox).reshape(-1, 1), np.array(oz).reshape(-1, 1),
+                           np.array(oc))
+    got = pp.propagate(inst)
+    exact = float(sum(Fraction(c) for letters, c in terms if all(v == "Z" for v in letters.values())))
+    assert exact == 1.0 + 2.0 ** -52
+    assert got.expect == exact

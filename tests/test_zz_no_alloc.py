@@ -41,6 +41,8 @@ def test_noalloc_expectation_matches_pp_expect_on_consecutive_calls():
                                   out.data_ptr(), stream)
         assert st == pp.PP_OK
         torch.cuda.synchronize()
+        # both round the same exact 128-bit total with the same routine
+        assert out.item() == ref, (out.item(), ref)
         assert abs(out.item() - ref) <= expect_tol((x, z, c))
 
 
@@ -51,3 +53,19 @@ def test_noalloc_rejects_more_terms_than_its_scratch_holds():
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     st = pp.pp_expect_noalloc(36, pp.NOALLOC_MAX_TERMS + 1, 1, 1, out.data_ptr(), None)
     assert st == pp.PP_ERR_CAPACITY
+
+
+def test_noalloc_out_of_range_coefficient_gives_nan():
+    """A coefficient outside the exact sum's range (|c| >= 2^32, or not
+    finite) makes the result NaN instead of a wrapped-around value."""
+    import math
+    import torch
+    from paper_2606_20441_b300 import build, pp
+    build.build()
+    for bad in (2.0 ** 33, float("inf"), float("nan")):
+        x_dev = torch.zeros(3, dtype=torch.int64, device="cuda")
+        c_dev = torch.tensor([0.5, bad, 0.25], dtype=torch.float64, device="cuda")
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        assert pp.pp_expect_noalloc(3, 3, x_dev.data_ptr(), c_dev.data_ptr(), out.data_ptr(), None) == pp.PP_OK
+        torch.cuda.synchronize()
+        assert math.isnan(out.item())
