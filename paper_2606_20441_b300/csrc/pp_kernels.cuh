@@ -651,7 +651,7 @@ __device__ __forceinline__ void load_gate_table(GateTab<W, T>& tab, const SubLay
 // buckets, or the list a smaller tier passed on); a bucket that does not fit is
 // passed to the next tier.
 template <int W, typename T, int NT>
-__global__ void __launch_bounds__(NT) k_process(StepParams p, int cap) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_process(StepParams p, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int ctl[8];
     __shared__ uint32_t s_b;

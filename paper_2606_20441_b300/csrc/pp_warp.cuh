@@ -324,7 +324,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
 }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(32 * WARP_TILE_WARPS) k_process_warp(StepParams p, int cap) {
+__global__ void __launch_bounds__(32 * WARP_TILE_WARPS, 5) k_process_warp(StepParams p, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ GateTab<W, T> tab;
     __shared__ int s_ctl[WARP_TILE_WARPS][8];
