@@ -172,13 +172,24 @@ typedef struct {
     int w_max;
 } pp_batch_item;
 
-/* Runs pp_propagate(handles[i], items[i]) for i < n, many at once: up to
- * max_threads host threads take items in order and drive their handles'
- * sub-layer loops, so the propagations overlap on the GPU.  Give every handle
- * its own stream (pp_options.cuda_stream) -- handles on one stream serialise.
- * Handles must be distinct and must not be used by other calls meanwhile.
- * status_out (optional, [n]) receives each item's status; the return value is
- * PP_OK when all succeeded, else the first failing item's status. */
+/* Runs pp_propagate(handles[i], items[i]) for i < n in lockstep: handles on
+ * one device with the same mask width and precision form a group whose
+ * propagations advance together, one fused sub-layer per lockstep step; each
+ * step launches every kernel once for the whole group (grid row = instance,
+ * each row reading its own launch parameters from device memory) and waits
+ * for the device once, so a group of n instances costs one host
+ * synchronisation per step instead of n.  The groups run one after another on
+ * the stream of their first handle (the other handles' streams are not used;
+ * the call returns after the device work is done).  Each instance keeps its
+ * own plan, layouts, capacity, truncation (eps, w_max, top-K) and counters:
+ * its result and statistics equal those of pp_propagate on the same handle,
+ * except that the optional orbit tiles and per-tier timing are not used.  An
+ * instance that fails (capacity, cancel) stops with its status; the others
+ * go on.  Handles must be distinct (else every status is PP_ERR_ARG) and not
+ * be used by other calls meanwhile.  max_threads is ignored (kept for
+ * binary compatibility).  status_out (optional, [n]) receives each item's
+ * status; the return value is PP_OK when all succeeded, else the first
+ * failing item's status. */
 pp_status pp_propagate_batch(int n, pp_handle* const* handles, const pp_batch_item* items,
                              int max_threads, pp_status* status_out);
 

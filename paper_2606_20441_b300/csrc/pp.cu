@@ -9,6 +9,8 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <memory>
+#include <tuple>
 #include <thread>
 #include <string>
 #include <vector>
@@ -648,15 +650,24 @@ cudaError_t prepare_kernel(const pp_handle* h, KernelFacts& f, K kernel, int thr
     return cudaSuccess;
 }
 
+// A tier launch covers one instance (ps == nullptr: the parameters passed by
+// value) or a batch: grid row y serves instance y with the parameters ps[y]
+// (device memory) and, in the global tier, the scratch scratch_of[y].
+struct LaunchRows {
+    const StepParams* ps = nullptr;
+    int n = 1;
+    unsigned char* const* scratch_of = nullptr;
+};
+
 template <int W, typename T, int NT>
-cudaError_t launch_smem_tier(pp_handle* h, const StepParams& p, int cap, uint32_t n_items) {
+cudaError_t launch_smem_tier(pp_handle* h, const StepParams& p, int cap, uint32_t n_items, const LaunchRows& rows) {
     const size_t smem = tile_layout_bytes<W, T, int16_t>((size_t)cap);
     static KernelFacts facts;   // shared by the threads of pp_propagate_batch
     int per_sm = 1;
     cudaError_t e = prepare_kernel(h, facts, k_process<W, T, NT>, NT, smem, &per_sm);
     if (e != cudaSuccess) return e;
     uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(per_sm * h->sm_count));
-    k_process<W, T, NT><<<grid, NT, smem, h->st>>>(p, cap);
+    k_process<W, T, NT><<<dim3(grid, rows.n), NT, smem, h->st>>>(p, rows.ps, cap);
     return cudaGetLastError();
 }
 
@@ -679,7 +690,7 @@ int tier_cap(const pp_handle* h, int tier);
 
 template <int W, typename T>
 cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orbit, uint32_t n_items,
-                           int* launches) {
+                           int* launches, const LaunchRows& rows) {
     ++*launches;
     const int cap = tier < kGlobalTier ? tier_cap(h, tier) : kTiers[tier].cap1;
     switch (tier) {
@@ -693,7 +704,7 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orb
                 if (e != cudaSuccess) return e;
                 uint32_t grid = std::min<uint32_t>(std::max<uint32_t>((n_items + ORB_WARPS - 1) / ORB_WARPS, 1),
                                                    (uint32_t)(per_sm * h->sm_count));
-                k_process_orbit<W, T><<<grid, 32 * ORB_WARPS, smem, h->st>>>(p, K);
+                k_process_orbit<W, T><<<dim3(grid, rows.n), 32 * ORB_WARPS, smem, h->st>>>(p, rows.ps, K);
                 return cudaGetLastError();
             }
             const size_t smem = warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS;
@@ -703,14 +714,15 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orb
             if (e != cudaSuccess) return e;
             uint32_t grid = std::min<uint32_t>(std::max<uint32_t>((n_items + WARP_TILE_WARPS - 1) / WARP_TILE_WARPS, 1),
                                                (uint32_t)(per_sm * h->sm_count));
-            k_process_warp<W, T><<<grid, kTiers[0].threads, smem, h->st>>>(p, cap);
+            k_process_warp<W, T><<<dim3(grid, rows.n), kTiers[0].threads, smem, h->st>>>(p, rows.ps, cap);
             return cudaGetLastError();
         }
-        case 1: return launch_smem_tier<W, T, kTiers[1].threads>(h, p, cap, n_items);
-        case 2: return launch_smem_tier<W, T, kTiers[2].threads>(h, p, cap, n_items);
+        case 1: return launch_smem_tier<W, T, kTiers[1].threads>(h, p, cap, n_items, rows);
+        case 2: return launch_smem_tier<W, T, kTiers[2].threads>(h, p, cap, n_items, rows);
         default: {
             uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)kFallbackCTAs);
-            k_process_global<W, T><<<grid, kTiers[kGlobalTier].threads, 0, h->st>>>(p, h->fb_scratch, h->fb_slice,
+            k_process_global<W, T><<<dim3(grid, rows.n), kTiers[kGlobalTier].threads, 0, h->st>>>(
+                p, rows.ps, h->fb_scratch, rows.scratch_of, h->fb_slice,
                                                                                   h->fb_cap);
             return cudaGetLastError();
         }
@@ -731,12 +743,12 @@ int tier_cap(const pp_handle* h, int tier) {
 }
 
 cudaError_t dispatch_process(pp_handle* h, const StepParams& p, int tier, bool orbit, uint32_t n_items,
-                             int* launches) {
+                             int* launches, const LaunchRows& rows = LaunchRows()) {
     bool f32 = h->opt.precision == PP_PRECISION_FP32;
-    if (h->W == 1) return f32 ? launch_process<1, float>(h, p, tier, orbit, n_items, launches)
-                              : launch_process<1, double>(h, p, tier, orbit, n_items, launches);
-    return f32 ? launch_process<2, float>(h, p, tier, orbit, n_items, launches)
-               : launch_process<2, double>(h, p, tier, orbit, n_items, launches);
+    if (h->W == 1) return f32 ? launch_process<1, float>(h, p, tier, orbit, n_items, launches, rows)
+                              : launch_process<1, double>(h, p, tier, orbit, n_items, launches, rows);
+    return f32 ? launch_process<2, float>(h, p, tier, orbit, n_items, launches, rows)
+               : launch_process<2, double>(h, p, tier, orbit, n_items, launches, rows);
 }
 
 // Load limit of a bucket of the orbit tier.
@@ -809,11 +821,12 @@ cudaError_t apply_noise(pp_handle* h, const NoiseHost& nh, int side, uint32_t B,
 // Groups the overflow strings of a freshly written layout by bucket.  Runs
 // whether or not anything spilled (the kernels find out on the device); the
 // number of grouped strings lands in counters[CTR_SPILL_TOTAL].
-cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, int* launches) {
-    cudaError_t e = cudaMemsetAsync(h->counters + CTR_SPILL_TOTAL, 0, sizeof(unsigned long long), h->st);
+cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, unsigned long long* counters,
+                        int* launches) {
+    cudaError_t e = cudaMemsetAsync(counters + CTR_SPILL_TOTAL, 0, sizeof(unsigned long long), h->st);
     if (e != cudaSuccess) return e;
     uint32_t grid = (nB + 1023) / 1024;
-    k_spill_offsets<<<grid, 1024, 0, h->st>>>(h->fill[side], nB, C, h->soff[side], h->counters + CTR_SPILL_TOTAL);
+    k_spill_offsets<<<grid, 1024, 0, h->st>>>(h->fill[side], nB, C, h->soff[side], counters + CTR_SPILL_TOTAL);
     const dim3 g2(NSPILL, (unsigned)std::max(1, h->sm_count * 8 / NSPILL));
     const bool f32 = h->opt.precision == PP_PRECISION_FP32;
     const Arena& r = h->spill_raw;
@@ -955,6 +968,510 @@ pp_status sort_result(pp_handle* h) {
         }
     h->res_side = cur;
     return PP_OK;
+}
+
+// ----------------------------------------------------------------------------- one propagation
+
+// The state of one propagation, advanced one fused sub-layer at a time.  A
+// single pp_propagate drives one; pp_propagate_batch drives many in lockstep,
+// launching each kernel once for all of them.
+struct Prop {
+    pp_handle* h = nullptr;
+    long long gen = 0;
+    std::chrono::steady_clock::time_point t0;
+    bool batch = false;              // part of a lockstep batch (no orbit tiles, no per-tier timing)
+    int S = 0, s = 0, side = 0, attempt = 0;
+    uint32_t B = 1, nB = 1;          // bucket counts of the source and destination layouts
+    uint64_t C = 0, nC = 0;          // their region sizes
+    size_t N = 0, peak = 0;
+    double updates = 0.0;
+    unsigned long long n_over_in = 0;   // grouped overflow strings of the source layout
+    std::map<int, double> growth;    // observed output/input per sub-layer kind
+    StepParams p;
+    pp_stats stats{};
+    int launches = 0;
+    FILE* trace = nullptr;
+    unsigned long long* ctr_dev = nullptr;   // the counters this propagation uses
+    unsigned long long ctr[CTR_COUNT];
+    float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
+    bool finished = false;
+    Prop() { std::memset(&p, 0, sizeof(p)); }
+    ~Prop() {
+        if (trace) fclose(trace);
+    }
+    Prop(const Prop&) = delete;
+    Prop& operator=(const Prop&) = delete;
+
+    double growth_of(int k) const {
+        auto it = growth.find(h->sub_kind[k]);
+        return it == growth.end() ? 3.0 : it->second;
+    }
+    // sub-layers processed by the orbit tiles first (the input observable,
+    // which may hold duplicates, and sub-layers after a forced first tier go
+    // to the sparse tiles)
+    bool use_orbit(int k) const {
+        const SubLayerDesc& d = h->subs[k];
+        return !batch && d.orb && !d.first && h->tune.orbit_tiles && h->tune.first_tier == 0;
+    }
+    // buckets for sub-layer k holding about n strings: a sparse tile must also
+    // hold the strings the sub-layer creates, so aim at cap / (headroom *
+    // growth); an orbit tile holds only its input (at 3/4 of its limit)
+    uint32_t buckets_for(int k, double n) const {
+        const double g = bucket_headroom(h) * std::max(1.0, growth_of(k));
+        double per = use_orbit(k) ? 0.75 * orbit_load_cap(h) : (double)tier_cap(h, 0) / g;
+        per = std::max(per, 16.0);
+        return pow2_at_least(n / per, h->fill_cap);
+    }
+};
+
+#undef CK
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, PP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+// Validates, plans, stages the observable and scatters it into the first
+// sub-layer's buckets (one synchronisation).
+pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, const uint64_t* oz,
+                     const double* oc, double eps, int w_max, unsigned long long* ctr_dev, bool batch) {
+    P.h = h;
+    P.batch = batch;
+    P.ctr_dev = ctr_dev;
+    h->err.clear();
+    P.t0 = std::chrono::steady_clock::now();
+    if (!h->have_circuit) return fail(h, PP_ERR_STATE, "no circuit loaded");
+    if (n_terms && (!ox || !oz || !oc)) return fail(h, PP_ERR_ARG, "null observable arrays");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(h, PP_ERR_ARG, "eps must be finite and >= 0");
+    h->have_result = false;
+    P.gen = ++h->run_gen;
+    pp_status st;
+    if (h->subs_dirty && (st = build_plan(h)) != PP_OK) return st;
+    if ((st = ensure_memory(h)) != PP_OK) return st;
+    if (!P.ctr_dev) P.ctr_dev = h->counters;
+    const int W = h->W;
+
+    // stage the observable
+    if (n_terms > h->cap) return fail(h, PP_ERR_CAPACITY, "observable larger than capacity");
+    size_t need = std::max<size_t>(n_terms, 1) * (2 * W + 1);
+    if (need > h->stage_cap) {
+        if (h->stage) dev_free(h, h->stage);
+        h->stage = static_cast<uint64_t*>(dev_alloc(h, need * 8));
+        if (!h->stage) {
+            h->stage_cap = 0;
+            return fail(h, PP_ERR_NOMEM, "staging allocation failed");
+        }
+        h->stage_cap = need;
+    }
+    uint64_t* sx = h->stage;
+    uint64_t* sz = h->stage + n_terms * W;
+    double* sc = reinterpret_cast<double*>(h->stage + 2 * n_terms * W);
+    if (n_terms) {
+        CK(cudaMemcpyAsync(sx, ox, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(sz, oz, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(sc, oc, n_terms * 8, cudaMemcpyHostToDevice, h->st));
+    }
+    if (const char* tp = getenv("PP_TRACE")) P.trace = fopen(tp, "a");
+    if (h->timing && !batch && !h->tier_ev[0][0])
+        for (auto& pr : h->tier_ev)
+            for (auto& e : pr) CK(cudaEventCreate(&e));
+
+    StepParams& p = P.p;
+    p.eps = eps;
+    p.eps_f = eps_float_ceil(eps);
+    p.w_max = w_max;
+    p.counters = P.ctr_dev;
+    p.rpx = h->spill_raw.x;
+    p.rpz = h->spill_raw.z;
+    p.rpc = h->spill_raw.c;
+    p.rpb = h->spill_b;
+    p.rps = h->spill_s;
+    p.rpcap = h->spill_cap;
+    p.spill_ctr = h->spill_ctr;
+    p.spx = h->spill_grp.x;
+    p.spz = h->spill_grp.z;
+    p.spc = h->spill_grp.c;
+    p.spcap = h->spill_cap;
+    p.phase = P.trace ? P.ctr_dev + CTR_PHASE : nullptr;
+    p.gcap = h->fb_cap;
+    p.gslice = h->fb_slice;
+
+    // scatter the input into the first sub-layer's buckets
+    P.side = 0;
+    P.B = P.buckets_for(0, (double)n_terms);
+    P.C = h->cap / P.B;
+    CK(cudaMemsetAsync(h->fill[0], 0, sizeof(uint32_t) * P.B, h->st));
+    CK(cudaMemsetAsync(P.ctr_dev, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+    CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
+    p.dx = h->arena[0].x;
+    p.dz = h->arena[0].z;
+    p.dc = h->arena[0].c;
+    p.dcap = h->cap;
+    p.dfill = h->fill[0];
+    p.dB = P.B;
+    p.dC = P.C;
+    p.next = h->d_subs;
+    if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, p, &P.launches));
+    CK(group_spill(h, 0, P.B, P.C, P.ctr_dev, &P.launches));
+    CK(cudaMemcpyAsync(P.ctr, P.ctr_dev, sizeof(P.ctr), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (P.ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input overflowed the overflow area");
+    P.n_over_in = P.ctr[CTR_SPILL_TOTAL];
+    P.N = P.peak = n_terms;
+    P.S = (int)h->subs.size();
+    P.s = 0;
+    P.attempt = 0;
+    return PP_OK;
+}
+
+// Plans sub-layer P.s: the destination buckets (unless a retry already sized
+// them) and the launch parameters.
+pp_status prop_setup(Prop& P) {
+    pp_handle* h = P.h;
+    const SubLayerDesc& d = h->subs[P.s];
+    const bool fin = d.final_ != 0;
+    if (P.attempt == 0) {
+        const double est = std::max(64.0, (double)P.N * P.growth_of(P.s) * 1.3);
+        P.nB = fin ? 1 : P.buckets_for(P.s + 1, est);
+        P.nC = fin ? h->cap : h->cap / P.nB;
+    }
+    StepParams& p = P.p;
+    p.sx = h->arena[P.side].x;
+    p.sz = h->arena[P.side].z;
+    p.sc = h->arena[P.side].c;
+    p.scap = h->cap;
+    p.sfill = h->fill[P.side];
+    p.soff = h->soff[P.side];
+    p.sB = P.B;
+    p.sC = P.C;
+    p.dx = h->arena[P.side ^ 1].x;
+    p.dz = h->arena[P.side ^ 1].z;
+    p.dc = h->arena[P.side ^ 1].c;
+    p.dcap = h->cap;
+    p.dfill = h->fill[P.side ^ 1];
+    p.dB = P.nB;
+    p.dC = P.nC;
+    p.desc = h->d_subs + P.s;
+    p.next = fin ? nullptr : h->d_subs + P.s + 1;
+    // A noise map on the input observable itself stays in the processor's
+    // prologue (after the merge and truncation of the input); any other is
+    // applied by a streaming pass over the layout first (prop_noise).
+    p.has_noise = d.noise >= 0 && d.first;
+    if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
+    return PP_OK;
+}
+
+// The streaming noise pass of sub-layer P.s (not again on a retry: it acts in place).
+pp_status prop_noise(Prop& P) {
+    pp_handle* h = P.h;
+    const SubLayerDesc& d = h->subs[P.s];
+    if (d.noise >= 0 && !d.first && P.attempt == 0)
+        CK(apply_noise(h, h->noise[d.noise], P.side, P.B, P.C, P.n_over_in, P.p.eps, P.p.eps_f, &P.launches));
+    return PP_OK;
+}
+
+// Launch parameters of tier `tier` of sub-layer P.s; returns whether tier 0
+// runs the orbit tiles, and the launch's work-item bound.
+bool prop_tier(Prop& P, int tier, uint32_t* n_items) {
+    pp_handle* h = P.h;
+    StepParams& p = P.p;
+    p.in_list = tier == 0 ? nullptr : h->pass_list[tier - 1];
+    p.n_list = 0;
+    p.n_list_dev = tier == 0 ? nullptr : P.ctr_dev + CTR_DEFER + tier - 1;
+    *n_items = tier == 0 ? P.B : UINT32_MAX;   // the later tiers' counts are on the device
+    p.out_list = tier < kGlobalTier ? h->pass_list[tier] : nullptr;
+    p.work_ctr = CTR_WORK + tier;
+    p.defer_ctr = CTR_DEFER + (tier < kGlobalTier ? tier : 0);
+    const bool orbit = tier == 0 && P.use_orbit(P.s);
+    p.max_load = (uint32_t)((tier == kGlobalTier ? h->fb_cap : tier_cap(h, tier)) * 3 / 4);
+    if (orbit) p.max_load = (uint32_t)orbit_load_cap(h);
+    if (tier < h->tune.first_tier) p.max_load = 0;   // every bucket is passed on
+    if (orbit) P.stats.orbit_launches++;
+    P.stats.tier_launches[tier]++;
+    return orbit;
+}
+
+// After the sub-layer's counters are back (P.ctr): statistics, errors, the
+// retry decision, top-K, and the move to the next sub-layer.
+pp_status prop_finish(Prop& P) {
+    pp_handle* h = P.h;
+    const int s = P.s;
+    const SubLayerDesc& d = h->subs[s];
+    const bool fin = d.final_ != 0;
+    const unsigned long long* ctr = P.ctr;
+    if (h->cancel_gen.load() == P.gen) return fail(h, PP_ERR_TIMEOUT, "cancelled after sub-layer %d", s);
+    for (int tier = 0; tier < N_TIERS; ++tier) {
+        P.stats.tier_ms[tier] += P.ms[tier];
+        P.stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];
+    }
+    unsigned long long passed[N_TIERS] = {ctr[CTR_DEFER], ctr[CTR_DEFER + 1], ctr[CTR_DEFER + 2], 0};
+    P.stats.fallback_buckets += (int)passed[kGlobalTier - 1];
+    if (ctr[CTR_ERR_FALLBACK])
+        return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s, h->fb_cap);
+    // A sub-layer whose output outgrew the planned buckets and the overflow area
+    // runs once more with buckets sized from its true output count: its source
+    // layout is only read, and its noise map (applied in place) is not applied again.
+    if (ctr[CTR_ERR_REGION] && !fin && P.attempt == 0 && ctr[CTR_OUT] <= h->cap) {
+        P.growth[h->sub_kind[s]] = std::max(0.05, (double)ctr[CTR_OUT] / std::max<double>(1.0, (double)P.N));
+        P.nB = P.buckets_for(s + 1, std::max(64.0, 1.3 * (double)ctr[CTR_OUT]));
+        P.nC = h->cap / P.nB;
+        P.stats.retries++;
+        P.attempt = 1;
+        return PP_OK;
+    }
+    if (ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap)
+        return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
+                    "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap, h->spill_cap);
+    const unsigned long long n_spill_out = fin ? 0ull : ctr[CTR_SPILL_TOTAL];
+    // canonical gate-by-gate count (live terms entering each gate in listed
+    // order), summed by the kernels over string lifetimes
+    P.updates += (double)ctr[CTR_UPDATES];
+    size_t Nout = (size_t)ctr[CTR_OUT];
+    P.peak = std::max(P.peak, Nout);
+    bool compacted = false;
+    if (h->top_k > 0 && d.layer_end && Nout > h->top_k) {
+        // keep the K largest strings of the layer's result (Sec. I.A)
+        if (!fin) {
+            CK(apply_top_k(h, P.side ^ 1, true, P.nB, P.nC, n_spill_out, &P.launches));
+        } else {
+            CK(apply_top_k(h, P.side ^ 1, false, 1, h->cap, Nout, &P.launches));
+            CK(compact_result(h, P.side ^ 1, Nout, &P.launches));
+            compacted = true;
+        }
+        Nout = h->top_k;
+    }
+    if (P.trace)
+        fprintf(P.trace,
+                "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"orbit\": %d, \"n_in\": %zu, \"n_out\": %zu, "
+                "\"buckets_in\": %u, \"buckets_out\": %u, \"passed\": [%llu, %llu, %llu], "
+                "\"spill\": %llu, \"ms\": [%.4f, %.4f, %.4f, %.4f], "
+                "\"tier_strings\": [%llu, %llu, %llu, %llu], "
+                "\"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
+                "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu]}\n",
+                s, d.cls, d.n_gates, (int)P.use_orbit(s), P.N, Nout, P.B, P.nB, passed[0], passed[1], passed[2],
+                n_spill_out, P.ms[0], P.ms[1], P.ms[2], P.ms[3],
+                ctr[CTR_LOADED] + ctr[CTR_EMITTED], ctr[CTR_LOADED + 1] + ctr[CTR_EMITTED + 1],
+                ctr[CTR_LOADED + 2] + ctr[CTR_EMITTED + 2], ctr[CTR_LOADED + 3] + ctr[CTR_EMITTED + 3],
+                ctr[CTR_FAIL], ctr[CTR_FAIL + 1], ctr[CTR_FAIL + 2], ctr[CTR_PHASE], ctr[CTR_PHASE + 1],
+                ctr[CTR_PHASE + 2], ctr[CTR_PHASE + 3], ctr[CTR_PHASE_CTA], ctr[CTR_PHASE_CTA + 1],
+                ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3]);
+    if (P.N > 0) P.growth[h->sub_kind[s]] = std::max(0.05, (double)Nout / (double)P.N);
+    P.N = Nout;
+    P.n_over_in = n_spill_out;
+    if (!compacted) P.side ^= 1;   // a compacted result went back to this sub-layer's source arena
+    P.B = P.nB;
+    P.C = P.nC;
+    P.stats.n_sublayers++;
+    for (float& m : P.ms) m = 0.f;
+    P.s++;
+    P.attempt = 0;
+    return PP_OK;
+}
+
+void prop_end(Prop& P) {
+    pp_handle* h = P.h;
+    h->res_side = P.side;
+    h->n_res = P.N;
+    h->have_result = true;
+    P.stats.n_terms = P.N;
+    P.stats.peak_terms = P.peak;
+    P.stats.updates = P.updates;
+    P.stats.kernel_launches = P.launches;
+    P.stats.bytes_per_string = (double)term_bytes(h);
+    P.stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - P.t0).count();
+    h->stats = P.stats;
+    P.finished = true;
+}
+
+// ----------------------------------------------------------------------------- lockstep batches
+
+// Device buffers of one lockstep batch.
+struct BatchBufs {
+    pp_handle* h = nullptr;
+    unsigned long long* ctr = nullptr;   // [n][CTR_COUNT]
+    StepParams* ps = nullptr;            // [N_TIERS][n]
+    SpillArgs* args = nullptr;           // [2][n]: clearing, overflow grouping
+    unsigned char** scratch = nullptr;   // [n] global-tier scratch of each instance
+    ~BatchBufs() {
+        for (void* q : {(void*)ctr, (void*)ps, (void*)args, (void*)scratch})
+            if (q) dev_free(h, q);
+    }
+};
+
+template <int W, typename T>
+void launch_spill_batch(pp_handle* h0, const SpillArgs* args, int rows) {
+    k_spill_offsets_batch<<<dim3((unsigned)std::max(1, h0->sm_count), rows), 1024, 0, h0->st>>>(args);
+    const dim3 g(NSPILL, (unsigned)std::max(1, h0->sm_count * 8 / NSPILL / std::max(1, rows)) + 1, rows);
+    k_spill_move_batch<W, T><<<g, 256, 0, h0->st>>>(args);
+}
+
+// Runs the propagations of handles[idx[..]] (same device, mask width and
+// precision) in lockstep on the first handle's stream: every lockstep step
+// advances each unfinished propagation by one fused sub-layer, launching each
+// kernel once for all of them (grid row = instance), and waits for the device
+// once for the whole batch.  Each instance keeps its own plan, layouts and
+// counters, so its result equals a pp_propagate of the same handle.
+void run_lockstep(pp_handle* const* handles, const pp_batch_item* items, const std::vector<int>& idx,
+                  std::vector<pp_status>& status) {
+    const int n = (int)idx.size();
+    pp_handle* h0 = handles[idx[0]];
+    pp_handle* h = h0;   // for CK-style error reports on the batch's own buffers
+    std::vector<cudaStream_t> saved(n);
+    for (int k = 0; k < n; ++k) {
+        saved[k] = handles[idx[k]]->st;
+        handles[idx[k]]->st = h0->st;
+    }
+    auto finish_all = [&](pp_status st) {
+        for (int k = 0; k < n; ++k)
+            if (status[idx[k]] == PP_OK) status[idx[k]] = st;
+    };
+    BatchBufs bb;
+    bb.h = h0;
+    bb.ctr = static_cast<unsigned long long*>(dev_alloc(h0, sizeof(unsigned long long) * CTR_COUNT * n));
+    bb.ps = static_cast<StepParams*>(dev_alloc(h0, sizeof(StepParams) * N_TIERS * n));
+    bb.args = static_cast<SpillArgs*>(dev_alloc(h0, sizeof(SpillArgs) * 2 * n));
+    bb.scratch = static_cast<unsigned char**>(dev_alloc(h0, sizeof(unsigned char*) * n));
+    if (!bb.ctr || !bb.ps || !bb.args || !bb.scratch) {
+        fail(h0, PP_ERR_NOMEM, "batch buffers allocation failed");
+        finish_all(PP_ERR_NOMEM);
+        for (int k = 0; k < n; ++k) handles[idx[k]]->st = saved[k];
+        return;
+    }
+    std::vector<std::unique_ptr<Prop>> props(n);
+    for (int k = 0; k < n; ++k) {
+        props[k].reset(new Prop());
+        const pp_batch_item& it = items[idx[k]];
+        const pp_status st = prop_begin(*props[k], handles[idx[k]], it.n_terms, it.ox, it.oz, it.oc, it.eps,
+                                        it.w_max, bb.ctr + (size_t)CTR_COUNT * k, true);
+        if (st != PP_OK) {
+            status[idx[k]] = st;
+            props[k]->finished = true;
+        } else if (props[k]->S == 0) {
+            prop_end(*props[k]);
+        }
+    }
+    const bool f32 = h0->opt.precision == PP_PRECISION_FP32;
+    std::vector<StepParams> ps_host((size_t)N_TIERS * n);
+    std::vector<SpillArgs> args_host((size_t)2 * n);
+    std::vector<unsigned char*> scratch_host(n);
+    std::vector<unsigned long long> ctr_host((size_t)CTR_COUNT * n);
+    std::vector<int> act;
+    for (;;) {
+        act.clear();
+        for (int k = 0; k < n; ++k)
+            if (!props[k]->finished) act.push_back(k);
+        if (act.empty()) break;
+        const int m = (int)act.size();
+        PP_RANGE_PUSH("pp lockstep step");
+        pp_status bad = PP_OK;
+        uint32_t max_zero = 1;
+        for (int a = 0; a < m; ++a) {
+            Prop& P = *props[act[a]];
+            prop_setup(P);
+            pp_handle* hk = P.h;
+            const bool fin = hk->subs[P.s].final_ != 0;
+            SpillArgs z{};
+            z.zero_fill = fin ? nullptr : hk->fill[P.side ^ 1];
+            z.zero_n = fin ? 0 : P.nB;
+            z.zero_shards = hk->spill_ctr;
+            z.zero_ctr = P.ctr_dev;
+            z.zero_ctr_n = CTR_COUNT;
+            args_host[a] = z;
+            max_zero = std::max(max_zero, z.zero_n);
+            SpillArgs g{};
+            g.fill = hk->fill[P.side ^ 1];
+            g.nB = fin ? 0 : P.nB;
+            g.C = P.nC;
+            g.soff = hk->soff[P.side ^ 1];
+            g.total = P.ctr_dev + CTR_SPILL_TOTAL;
+            g.rx = hk->spill_raw.x;
+            g.rz = hk->spill_raw.z;
+            g.rc = hk->spill_raw.c;
+            g.rb = hk->spill_b;
+            g.rs = hk->spill_s;
+            g.rcap = hk->spill_cap;
+            g.shard_fill = hk->spill_ctr;
+            g.ox = hk->spill_grp.x;
+            g.oz = hk->spill_grp.z;
+            g.oc = hk->spill_grp.c;
+            g.ocap = hk->spill_cap;
+            args_host[m + a] = g;
+            scratch_host[a] = hk->fb_scratch;
+        }
+        cudaError_t e = cudaMemcpyAsync(bb.args, args_host.data(), sizeof(SpillArgs) * 2 * m,
+                                        cudaMemcpyHostToDevice, h0->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bb.scratch, scratch_host.data(), sizeof(unsigned char*) * m, cudaMemcpyHostToDevice,
+                                h0->st);
+        if (e == cudaSuccess) {
+            k_clear<<<dim3((unsigned)std::min<uint32_t>((max_zero + 255) / 256, 4u * h0->sm_count), m), 256, 0,
+                      h0->st>>>(bb.args);
+            e = cudaGetLastError();
+        }
+        for (int a = 0; a < m && e == cudaSuccess; ++a)
+            if (prop_noise(*props[act[a]]) != PP_OK) e = cudaErrorUnknown;
+        for (int tier = 0; tier < N_TIERS && e == cudaSuccess; ++tier) {
+            uint32_t bound = 1;
+            for (int a = 0; a < m; ++a) {
+                uint32_t ni;
+                prop_tier(*props[act[a]], tier, &ni);
+                bound = std::max(bound, ni);
+                ps_host[(size_t)tier * n + a] = props[act[a]]->p;
+            }
+            e = cudaMemcpyAsync(bb.ps + (size_t)tier * n, ps_host.data() + (size_t)tier * n, sizeof(StepParams) * m,
+                                cudaMemcpyHostToDevice, h0->st);
+            if (e != cudaSuccess) break;
+            LaunchRows rows;
+            rows.ps = bb.ps + (size_t)tier * n;
+            rows.n = m;
+            rows.scratch_of = bb.scratch;
+            int dummy = 0;
+            e = dispatch_process(h0, props[act[0]]->p, tier, false, bound, &dummy, rows);
+        }
+        if (e == cudaSuccess) {
+            if (h0->W == 1) {
+                if (f32) launch_spill_batch<1, float>(h0, bb.args + m, m);
+                else launch_spill_batch<1, double>(h0, bb.args + m, m);
+            } else {
+                if (f32) launch_spill_batch<2, float>(h0, bb.args + m, m);
+                else launch_spill_batch<2, double>(h0, bb.args + m, m);
+            }
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            // the active instances' counters are scattered over the batch array
+            e = cudaMemcpyAsync(ctr_host.data(), bb.ctr, sizeof(unsigned long long) * CTR_COUNT * n,
+                                cudaMemcpyDeviceToHost, h0->st);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h0->st);
+        PP_RANGE_POP();
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(h, PP_ERR_CUDA, "lockstep batch step failed: %s", cudaGetErrorString(e));
+            bad = PP_ERR_CUDA;
+        }
+        for (int a = 0; a < m; ++a) {
+            Prop& P = *props[act[a]];
+            if (bad != PP_OK) {
+                status[idx[act[a]]] = bad;
+                P.finished = true;
+                continue;
+            }
+            const size_t k = (size_t)act[a];
+            std::memcpy(P.ctr, ctr_host.data() + (size_t)CTR_COUNT * k, sizeof(P.ctr));
+            P.launches += 2 + N_TIERS;   // this instance's rows of the step's launches
+            const pp_status st = prop_finish(P);
+            if (st != PP_OK) {
+                status[idx[act[a]]] = st;
+                P.finished = true;
+            } else if (P.s == P.S) {
+                prop_end(P);
+            }
+        }
+    }
+    cudaStreamSynchronize(h0->st);
+    for (int k = 0; k < n; ++k) handles[idx[k]]->st = saved[k];
 }
 
 }  // namespace
@@ -1201,270 +1718,38 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
 pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const uint64_t* oz,
                        const double* oc, double eps, int w_max) {
     if (!h) return PP_ERR_ARG;
-    h->err.clear();
-    auto t0 = std::chrono::steady_clock::now();
-    if (!h->have_circuit) return fail(h, PP_ERR_STATE, "no circuit loaded");
-    if (n_terms && (!ox || !oz || !oc)) return fail(h, PP_ERR_ARG, "null observable arrays");
-    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(h, PP_ERR_ARG, "eps must be finite and >= 0");
-    h->have_result = false;
-    const long long gen = ++h->run_gen;
-    pp_status st;
-    if (h->subs_dirty && (st = build_plan(h)) != PP_OK) return st;
-    if ((st = ensure_memory(h)) != PP_OK) return st;
-    const int W = h->W;
-    int launches = 0;
-    pp_stats stats{};
-
-    // stage the observable
-    if (n_terms > h->cap) return fail(h, PP_ERR_CAPACITY, "observable larger than capacity");
-    size_t need = std::max<size_t>(n_terms, 1) * (2 * W + 1);
-    if (need > h->stage_cap) {
-        if (h->stage) dev_free(h, h->stage);
-        h->stage = static_cast<uint64_t*>(dev_alloc(h, need * 8));
-        if (!h->stage) return fail(h, PP_ERR_NOMEM, "staging allocation failed");
-        h->stage_cap = need;
-    }
-    uint64_t* sx = h->stage;
-    uint64_t* sz = h->stage + n_terms * W;
-    double* sc = reinterpret_cast<double*>(h->stage + 2 * n_terms * W);
-    if (n_terms) {
-        CK(cudaMemcpyAsync(sx, ox, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
-        CK(cudaMemcpyAsync(sz, oz, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
-        CK(cudaMemcpyAsync(sc, oc, n_terms * 8, cudaMemcpyHostToDevice, h->st));
-    }
-
-    struct Scope {
-        FILE* trace = nullptr;
-        ~Scope() {
-            if (trace) fclose(trace);
-        }
-    } scope;
-    if (const char* tp = getenv("PP_TRACE")) scope.trace = fopen(tp, "a");
-    FILE* trace = scope.trace;
-    unsigned long long* phase = nullptr;
-    if (trace) {
-        phase = h->counters + CTR_PHASE;
-    }
-    if (h->timing && !h->tier_ev[0][0])
-        for (auto& pr : h->tier_ev)
-            for (auto& e : pr) CK(cudaEventCreate(&e));
-
-    const size_t tcap = (size_t)tier_cap(h, 0);
-    std::map<int, double> growth;   // observed output/input per sub-layer kind
-    auto growth_of = [&](int s) {
-        auto it = growth.find(h->sub_kind[s]);
-        return it == growth.end() ? 3.0 : it->second;
-    };
-    // buckets for sub-layer s holding about n strings: its tile must also hold
-    // the strings the sub-layer creates, so aim at tcap / (headroom * growth)
-    const double headroom = bucket_headroom(h);
-    // sub-layers processed by the orbit tier first (the input observable, which
-    // may hold duplicates, and sub-layers after a forced first tier go to the
-    // sparse tiers)
-    auto use_orbit = [&](int s) {
-        const SubLayerDesc& d = h->subs[s];
-        return d.orb && !d.first && h->tune.orbit_tiles && h->tune.first_tier == 0;
-    };
-    // an orbit bucket holds its input strings; the strings it creates live in
-    // its coefficient pool, so only the input is planned (at 3/4 of the limit)
-    const double ocap = 0.75 * orbit_load_cap(h);
-    auto buckets_for = [&](int s, double n) {
-        const double g = headroom * std::max(1.0, growth_of(s));
-        double per = use_orbit(s) ? ocap : (double)tcap / g;
-        per = std::max(per, 16.0);
-        return pow2_at_least(n / per, h->fill_cap);
-    };
-
-    StepParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.eps = eps;
-    p.eps_f = eps_float_ceil(eps);
-    p.w_max = w_max;
-    p.counters = h->counters;
-    p.rpx = h->spill_raw.x;
-    p.rpz = h->spill_raw.z;
-    p.rpc = h->spill_raw.c;
-    p.rpb = h->spill_b;
-    p.rps = h->spill_s;
-    p.rpcap = h->spill_cap;
-    p.spill_ctr = h->spill_ctr;
-    p.spx = h->spill_grp.x;
-    p.spz = h->spill_grp.z;
-    p.spc = h->spill_grp.c;
-    p.spcap = h->spill_cap;
-    p.phase = phase;
-
-    // scatter the input into the first sub-layer's buckets
-    int side = 0;
-    uint32_t B = buckets_for(0, (double)n_terms);
-    uint64_t C = h->cap / B;
-    unsigned long long ctr[CTR_COUNT];
-    CK(cudaMemsetAsync(h->fill[side], 0, sizeof(uint32_t) * B, h->st));
-    CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
-    CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
-    p.dx = h->arena[side].x;
-    p.dz = h->arena[side].z;
-    p.dc = h->arena[side].c;
-    p.dcap = h->cap;
-    p.dfill = h->fill[side];
-    p.dB = B;
-    p.dC = C;
-    p.next = h->d_subs;
-    if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, p, &launches));
-    CK(group_spill(h, side, B, C, &launches));
-    CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    if (ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input overflowed the overflow area");
-    unsigned long long n_over_in = ctr[CTR_SPILL_TOTAL];   // grouped overflow strings of the current layout
-
+    Prop P;
+    pp_status st = prop_begin(P, h, n_terms, ox, oz, oc, eps, w_max, h->counters, false);
+    if (st != PP_OK) return st;
     // One host synchronisation per sub-layer: the tiers after the first read
     // their work counts from the device (the previous tier's deferral
     // counter), the overflow grouping always runs, and the counters come back
     // in one copy at the end.
-    size_t N = n_terms;
-    size_t peak = N;
-    double updates = 0.0;
-    const int S = (int)h->subs.size();
-    for (int s = 0; s < S; ++s) {
-        const SubLayerDesc& d = h->subs[s];
-        const bool fin = d.final_ != 0;
-        const int kind = h->sub_kind[s];
-        double est = std::max(64.0, (double)N * growth_of(s) * 1.3);
-        uint32_t nB = fin ? 1 : buckets_for(s + 1, est);
-        uint64_t nC = fin ? h->cap : h->cap / nB;
-        // A sub-layer whose output outgrew the planned buckets and the overflow
-        // area runs once more with buckets sized from its true output count:
-        // its source layout is only read, and its noise map (applied in place)
-        // is not applied again.
-        float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
-        unsigned long long passed[N_TIERS] = {0, 0, 0, 0};   // buckets tier t handed to t+1
-        for (int attempt = 0;; ++attempt) {
+    while (P.s < P.S) {
+        if ((st = prop_setup(P)) != PP_OK) return st;
         PP_RANGE_PUSH("pp sub-layer");
-        if (!fin) CK(cudaMemsetAsync(h->fill[side ^ 1], 0, sizeof(uint32_t) * nB, h->st));
-        CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
+        const bool fin = h->subs[P.s].final_ != 0;
+        if (!fin) CK(cudaMemsetAsync(h->fill[P.side ^ 1], 0, sizeof(uint32_t) * P.nB, h->st));
+        CK(cudaMemsetAsync(P.ctr_dev, 0, sizeof(unsigned long long) * CTR_COUNT, h->st));
         CK(cudaMemsetAsync(h->spill_ctr, 0, sizeof(unsigned long long) * NSPILL, h->st));
-        p.sx = h->arena[side].x;
-        p.sz = h->arena[side].z;
-        p.sc = h->arena[side].c;
-        p.scap = h->cap;
-        p.sfill = h->fill[side];
-        p.soff = h->soff[side];
-        p.sB = B;
-        p.sC = C;
-        p.dx = h->arena[side ^ 1].x;
-        p.dz = h->arena[side ^ 1].z;
-        p.dc = h->arena[side ^ 1].c;
-        p.dcap = h->cap;
-        p.dfill = h->fill[side ^ 1];
-        p.dB = nB;
-        p.dC = nC;
-        p.desc = h->d_subs + s;
-        p.next = fin ? nullptr : h->d_subs + s + 1;
-        // A noise map on the input observable itself stays in the processor's
-        // prologue (after the merge and truncation of the input); any other is
-        // applied by a streaming pass over the layout first.
-        p.has_noise = d.noise >= 0 && d.first;
-        if (p.has_noise) p.noise = noise_desc(h->noise[d.noise]);
-        if (d.noise >= 0 && !d.first && attempt == 0)
-            CK(apply_noise(h, h->noise[d.noise], side, B, C, n_over_in, p.eps, p.eps_f, &launches));
+        if ((st = prop_noise(P)) != PP_OK) return st;
         for (int tier = 0; tier < N_TIERS; ++tier) {
-            p.in_list = tier == 0 ? nullptr : h->pass_list[tier - 1];
-            p.n_list = 0;
-            p.n_list_dev = tier == 0 ? nullptr : h->counters + CTR_DEFER + tier - 1;
-            const uint32_t n_items = tier == 0 ? B : UINT32_MAX;   // launch bound; the count is on the device
-            p.out_list = tier < kGlobalTier ? h->pass_list[tier] : nullptr;
-            p.work_ctr = CTR_WORK + tier;
-            p.defer_ctr = CTR_DEFER + (tier < kGlobalTier ? tier : 0);
-            const bool orbit = tier == 0 && use_orbit(s);
-            p.max_load = (uint32_t)((tier == kGlobalTier ? h->fb_cap : tier_cap(h, tier)) * 3 / 4);
-            if (orbit) p.max_load = (uint32_t)orbit_load_cap(h);
-            if (tier < h->tune.first_tier) p.max_load = 0;   // every bucket is passed on
+            uint32_t n_items;
+            const bool orbit = prop_tier(P, tier, &n_items);
             if (h->timing) CK(cudaEventRecord(h->tier_ev[tier][0], h->st));
-            CK(dispatch_process(h, p, tier, orbit, n_items, &launches));
+            CK(dispatch_process(h, P.p, tier, orbit, n_items, &P.launches));
             if (h->timing) CK(cudaEventRecord(h->tier_ev[tier][1], h->st));
-            if (orbit) stats.orbit_launches++;
-            stats.tier_launches[tier]++;
         }
-        if (!fin) CK(group_spill(h, side ^ 1, nB, nC, &launches));
-        CK(cudaMemcpyAsync(ctr, h->counters, sizeof(ctr), cudaMemcpyDeviceToHost, h->st));
+        if (!fin) CK(group_spill(h, P.side ^ 1, P.nB, P.nC, P.ctr_dev, &P.launches));
+        CK(cudaMemcpyAsync(P.ctr, P.ctr_dev, sizeof(P.ctr), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         PP_RANGE_POP();
-        if (h->cancel_gen.load() == gen) return fail(h, PP_ERR_TIMEOUT, "cancelled after sub-layer %d", s);
-        for (int tier = 0; tier < N_TIERS; ++tier) {
-            ms[tier] = 0.f;
-            if (h->timing) CK(cudaEventElapsedTime(&ms[tier], h->tier_ev[tier][0], h->tier_ev[tier][1]));
-            stats.tier_ms[tier] += ms[tier];
-            stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];
-        }
-        for (int tier = 0; tier < kGlobalTier; ++tier) passed[tier] = ctr[CTR_DEFER + tier];
-        stats.fallback_buckets += (int)passed[kGlobalTier - 1];
-        if (ctr[CTR_ERR_FALLBACK])
-            return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s,
-                        h->fb_cap);
-        if (ctr[CTR_ERR_REGION] && !fin && attempt == 0 && ctr[CTR_OUT] <= h->cap) {
-            growth[kind] = std::max(0.05, (double)ctr[CTR_OUT] / std::max<double>(1.0, (double)N));
-            nB = buckets_for(s + 1, std::max(64.0, 1.3 * (double)ctr[CTR_OUT]));
-            nC = h->cap / nB;
-            stats.retries++;
-            continue;
-        }
-        break;
-        }
-        if (ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap)
-            return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
-                        "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap,
-                        h->spill_cap);
-        const unsigned long long n_spill_out = fin ? 0ull : ctr[CTR_SPILL_TOTAL];
-        // canonical gate-by-gate count (live terms entering each gate in listed
-        // order), summed by the kernels over string lifetimes
-        updates += (double)ctr[CTR_UPDATES];
-        size_t Nout = (size_t)ctr[CTR_OUT];
-        peak = std::max(peak, Nout);
-        bool compacted = false;
-        if (h->top_k > 0 && d.layer_end && Nout > h->top_k) {
-            // keep the K largest strings of the layer's result (Sec. I.A)
-            if (!fin) {
-                CK(apply_top_k(h, side ^ 1, true, nB, nC, n_spill_out, &launches));
-            } else {
-                CK(apply_top_k(h, side ^ 1, false, 1, h->cap, Nout, &launches));
-                CK(compact_result(h, side ^ 1, Nout, &launches));
-                compacted = true;
-            }
-            Nout = h->top_k;
-        }
-        if (trace)
-            fprintf(trace,
-                    "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"orbit\": %d, \"n_in\": %zu, \"n_out\": %zu, "
-                    "\"buckets_in\": %u, \"buckets_out\": %u, \"passed\": [%llu, %llu, %llu], "
-                    "\"spill\": %llu, \"ms\": [%.4f, %.4f, %.4f, %.4f], "
-                    "\"tier_strings\": [%llu, %llu, %llu, %llu], "
-                    "\"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
-                    "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu]}\n",
-                    s, d.cls, d.n_gates, (int)use_orbit(s), N, Nout, B, nB, passed[0], passed[1], passed[2],
-                    n_spill_out, ms[0], ms[1], ms[2], ms[3],
-                    ctr[CTR_LOADED] + ctr[CTR_EMITTED], ctr[CTR_LOADED + 1] + ctr[CTR_EMITTED + 1],
-                    ctr[CTR_LOADED + 2] + ctr[CTR_EMITTED + 2], ctr[CTR_LOADED + 3] + ctr[CTR_EMITTED + 3],
-                    ctr[CTR_FAIL], ctr[CTR_FAIL + 1],
-                    ctr[CTR_FAIL + 2], ctr[CTR_PHASE], ctr[CTR_PHASE + 1], ctr[CTR_PHASE + 2], ctr[CTR_PHASE + 3],
-                    ctr[CTR_PHASE_CTA], ctr[CTR_PHASE_CTA + 1], ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3]);
-        if (N > 0) growth[kind] = std::max(0.05, (double)Nout / (double)N);
-        N = Nout;
-        n_over_in = n_spill_out;
-        if (!compacted) side ^= 1;   // a compacted result went back to this sub-layer's source arena
-        B = nB;
-        C = nC;
-        stats.n_sublayers++;
+        if (h->timing)
+            for (int tier = 0; tier < N_TIERS; ++tier)
+                CK(cudaEventElapsedTime(&P.ms[tier], h->tier_ev[tier][0], h->tier_ev[tier][1]));
+        if ((st = prop_finish(P)) != PP_OK) return st;
     }
-    h->res_side = side;
-    h->n_res = N;
-    h->have_result = true;
-    stats.n_terms = N;
-    stats.peak_terms = peak;
-    stats.updates = updates;
-    stats.kernel_launches = launches;
-    stats.bytes_per_string = (double)term_bytes(h);
-    stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    h->stats = stats;
+    prop_end(P);
     return PP_OK;
 }
 
@@ -1538,28 +1823,33 @@ pp_status pp_export_terms(pp_handle* h, size_t cap, uint64_t* x, uint64_t* z, do
 pp_status pp_propagate_batch(int n, pp_handle* const* handles, const pp_batch_item* items, int max_threads,
                              pp_status* status_out) {
     if (n < 0 || (n > 0 && (!handles || !items))) return PP_ERR_ARG;
+    bool bad = false;
     for (int i = 0; i < n; ++i)
-        if (!handles[i]) return PP_ERR_ARG;
+        if (!handles[i]) bad = true;
+    // a handle may appear once: its layouts hold one propagation
+    std::vector<const pp_handle*> sorted(handles, handles + n);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) bad = true;
+    if (bad) {
+        if (status_out)
+            for (int i = 0; i < n; ++i) status_out[i] = PP_ERR_ARG;
+        return PP_ERR_ARG;
+    }
     std::vector<pp_status> st(n, PP_OK);
-    std::atomic<int> next(0);
-    auto worker = [&]() {
-        for (;;) {
-            const int i = next.fetch_add(1);
-            if (i >= n) return;
-            pp_handle* h = handles[i];
-            if (cudaSetDevice(h->device) != cudaSuccess) {
-                cudaGetLastError();
-                st[i] = PP_ERR_CUDA;
-                continue;
-            }
-            const pp_batch_item& it = items[i];
-            st[i] = pp_propagate(h, it.n_terms, it.ox, it.oz, it.oc, it.eps, it.w_max);
+    // Handles that share a device, a mask width and a precision run in lockstep
+    // (run_lockstep); the groups run one after another.
+    std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+    for (int i = 0; i < n; ++i)
+        groups[std::make_tuple(handles[i]->device, handles[i]->W, handles[i]->opt.precision)].push_back(i);
+    (void)max_threads;   // lockstep groups need no host threads
+    for (auto& kv : groups) {
+        if (cudaSetDevice(std::get<0>(kv.first)) != cudaSuccess) {
+            cudaGetLastError();
+            for (int i : kv.second) st[i] = PP_ERR_CUDA;
+            continue;
         }
-    };
-    const int nt = std::max(1, std::min(n, max_threads > 0 ? max_threads : 16));
-    std::vector<std::thread> pool;
-    for (int k = 0; k < nt; ++k) pool.emplace_back(worker);
-    for (auto& t : pool) t.join();
+        run_lockstep(handles, items, kv.second, st);
+    }
     pp_status first = PP_OK;
     for (int i = 0; i < n; ++i) {
         if (status_out) status_out[i] = st[i];

@@ -59,6 +59,8 @@ struct StepParams {
     int work_ctr;                 // counter index of this launch's work queue
     int defer_ctr;                // counter index of out_list's length
     uint32_t max_load;            // buckets with more strings are passed on
+    int gcap;                     // global tier: strings per tile
+    uint64_t gslice;              // global tier: bytes per CTA slice of its scratch
     unsigned long long* phase;    // [4] cycles spent in load, prologue, rounds, output (tier 0),
                                   // accumulated when tracing; nullptr otherwise
 };
@@ -86,6 +88,22 @@ __device__ __forceinline__ uint32_t work_items(const StepParams& p) {
     if (!p.in_list) return p.sB;
     if (p.n_list_dev) return (uint32_t)*(volatile const unsigned long long*)p.n_list_dev;
     return p.n_list;
+}
+
+// A batched launch runs one instance per grid row: CTA row y takes the
+// parameters ps[y] (each instance has its own layouts, counters and work
+// queues); a plain launch passes ps = nullptr and its own parameters.  The
+// CTA copies its parameters to shared memory once.  Returns, for the whole
+// CTA, whether the launch's work queue still holds items (its claim counter
+// only grows, so a CTA that finds it exhausted can leave before setting up).
+__device__ __forceinline__ bool load_params(StepParams& dst, const StepParams& p, const StepParams* ps) {
+    __shared__ int s_left;
+    if (threadIdx.x == 0) {
+        dst = ps ? ps[blockIdx.y] : p;
+        s_left = *(volatile const unsigned long long*)&dst.counters[dst.work_ctr] < (unsigned long long)work_items(dst);
+    }
+    __syncthreads();
+    return s_left != 0;
 }
 
 constexpr int N_TIERS = 4;
@@ -255,7 +273,9 @@ template <>
 __device__ __forceinline__ float eps_of<float>(const StepParams& p) { return p.eps_f; }
 
 // Appends a string to bucket nb of the destination layout: into the bucket's
-// region while it has room, else into the overflow area.
+// region while it has room, else into the overflow area: the warp's own
+// shard, or, when that one is full, the next shards in turn (a shard's
+// counter may pass its capacity; readers clamp it).
 template <int W, typename T>
 __device__ __forceinline__ void emit(const StepParams& p, uint32_t nb, const uint64_t* x,
                                      const uint64_t* z, T c) {
@@ -271,9 +291,10 @@ __device__ __forceinline__ void emit(const StepParams& p, uint32_t nb, const uin
         return;
     }
     const uint64_t shard_cap = p.rpcap / NSPILL;
-    const int shard = (int)((blockIdx.x * 8 + (threadIdx.x >> 5)) % NSPILL);
-    unsigned long long k = atomicAdd(&p.spill_ctr[shard], 1ull);
-    if (k < shard_cap) {
+    int shard = (int)((blockIdx.x * 8 + (threadIdx.x >> 5)) % NSPILL);
+    for (int tries = 0; tries < NSPILL; ++tries, shard = (shard + 1) % NSPILL) {
+        unsigned long long k = atomicAdd(&p.spill_ctr[shard], 1ull);
+        if (k >= shard_cap) continue;
         k += (unsigned long long)shard * shard_cap;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -283,9 +304,9 @@ __device__ __forceinline__ void emit(const StepParams& p, uint32_t nb, const uin
         static_cast<T*>(p.rpc)[k] = c;
         p.rpb[k] = nb;
         p.rps[k] = slot - (uint32_t)p.dC;
-    } else {
-        atomicAdd(&p.counters[CTR_ERR_REGION], 1ull);
+        return;
     }
+    atomicAdd(&p.counters[CTR_ERR_REGION], 1ull);
 }
 
 // Processes one bucket: load, prologue (merge/truncate the input observable,
@@ -651,12 +672,14 @@ __device__ __forceinline__ void load_gate_table(GateTab<W, T>& tab, const SubLay
 // buckets, or the list a smaller tier passed on); a bucket that does not fit is
 // passed to the next tier.
 template <int W, typename T, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_process(StepParams p, int cap) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_process(const StepParams p0, const StepParams* ps, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int ctl[8];
     __shared__ uint32_t s_b;
     __shared__ GateTab<W, T> tab;
     __shared__ ActDesc s_ad, s_adn;
+    __shared__ StepParams p;
+    if (!load_params(p, p0, ps)) return;
     Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem, cap, ctl);
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
     if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
@@ -687,13 +710,21 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_process(StepParams p, int cap
 // Global tier for the largest buckets: the same processor with the tile in a
 // per-CTA slice of global scratch memory.
 template <int W, typename T>
-__global__ void __launch_bounds__(NWARPS * 32) k_process_global(StepParams p, unsigned char* scratch,
+__global__ void __launch_bounds__(NWARPS * 32) k_process_global(const StepParams p0, const StepParams* ps,
+                                                                unsigned char* scratch, unsigned char* const* scratch_of,
                                                                 size_t slice_bytes, int cap) {
     __shared__ int ctl[8];
     __shared__ uint32_t s_k;
     __shared__ GateTab<W, T> tab;
     __shared__ ActDesc s_ad, s_adn;
-    Tile<W, T, int32_t> t = carve_tile<W, T, int32_t>(scratch + slice_bytes * blockIdx.x, cap, ctl);
+    __shared__ StepParams p;
+    if (!load_params(p, p0, ps)) return;
+    // the global-tier slices: the launch's own, or in a batched launch those of
+    // instance y (scratch_of[y]), one per CTA column
+    unsigned char* base = scratch_of ? scratch_of[blockIdx.y] : scratch;
+    (void)slice_bytes;
+    (void)cap;
+    Tile<W, T, int32_t> t = carve_tile<W, T, int32_t>(base + p.gslice * blockIdx.x, p.gcap, ctl);
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
     if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
     load_gate_table<W, T>(tab, *p.desc);
@@ -732,6 +763,45 @@ __global__ void k_scatter_input(const uint64_t* ox, const uint64_t* oz, const do
     }
 }
 
+// Arguments of the overflow grouping of one layout (batched launches take an
+// array, one per grid row / slice).
+struct SpillArgs {
+    const uint32_t* fill;
+    uint32_t nB;
+    uint64_t C;
+    uint64_t* soff;
+    unsigned long long* total;
+    const uint64_t* rx;
+    const uint64_t* rz;
+    const void* rc;
+    const uint32_t* rb;
+    const uint32_t* rs;
+    uint64_t rcap;
+    const unsigned long long* shard_fill;
+    uint64_t* ox;
+    uint64_t* oz;
+    void* oc;
+    uint64_t ocap;
+    // zeroing at the start of a sub-layer (k_clear): the destination fill
+    // counters [0, zero_n), the overflow shard counters, and the counters
+    uint32_t* zero_fill;
+    uint32_t zero_n;
+    unsigned long long* zero_shards;
+    unsigned long long* zero_ctr;
+    int zero_ctr_n;
+};
+
+// Zeroes, for instance blockIdx.y, what a sub-layer starts from.
+__global__ void k_clear(const SpillArgs* a) {
+    const SpillArgs& s = a[blockIdx.y];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < s.zero_n; i += gridDim.x * blockDim.x)
+        s.zero_fill[i] = 0u;
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < NSPILL; i += blockDim.x) s.zero_shards[i] = 0ull;
+        for (int i = threadIdx.x; i < s.zero_ctr_n; i += blockDim.x) s.zero_ctr[i] = 0ull;
+    }
+}
+
 // Overflow bookkeeping: each bucket whose count exceeds its region gets a
 // contiguous range of the grouped overflow area.
 __global__ void k_spill_offsets(const uint32_t* fill, uint32_t nB, uint64_t C, uint64_t* soff,
@@ -756,6 +826,52 @@ __global__ void k_spill_offsets(const uint32_t* fill, uint32_t nB, uint64_t C, u
 
 // Grid (NSPILL, Y): blocks (s, y) move shard s's strings y*256 + t, stepping
 // by Y*256, up to the shard's fill (nothing to do when nothing spilled).
+// Batched k_spill_offsets: instance blockIdx.y (its `total` must start at 0).
+__global__ void k_spill_offsets_batch(const SpillArgs* a) {
+    __shared__ unsigned long long s_scan[1024];
+    __shared__ unsigned long long s_base;
+    const SpillArgs& s = a[blockIdx.y];
+    for (uint32_t b0 = blockIdx.x * blockDim.x; b0 < s.nB; b0 += gridDim.x * blockDim.x) {
+        const uint32_t b = b0 + threadIdx.x;
+        unsigned long long ex = 0;
+        if (b < s.nB && (uint64_t)s.fill[b] > s.C) ex = (uint64_t)s.fill[b] - s.C;
+        s_scan[threadIdx.x] = ex;
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            unsigned long long v = (int)threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0ull;
+            __syncthreads();
+            s_scan[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (threadIdx.x == blockDim.x - 1) s_base = atomicAdd(s.total, s_scan[threadIdx.x]);
+        __syncthreads();
+        if (b < s.nB) s.soff[b] = s_base + s_scan[threadIdx.x] - ex;
+        __syncthreads();
+    }
+}
+
+// Batched k_spill_move: grid (NSPILL, Y, instances).
+template <int W, typename T>
+__global__ void k_spill_move_batch(const SpillArgs* a) {
+    const SpillArgs& s = a[blockIdx.z];
+    const uint64_t shard_cap = s.rcap / NSPILL;
+    const uint64_t sh = blockIdx.x;
+    const uint64_t fill = s.shard_fill[sh] < shard_cap ? s.shard_fill[sh] : shard_cap;
+    const T* rc = static_cast<const T*>(s.rc);
+    T* oc = static_cast<T*>(s.oc);
+    for (uint64_t j = blockIdx.y * (uint64_t)blockDim.x + threadIdx.x; j < fill; j += (uint64_t)gridDim.y * blockDim.x) {
+        const uint64_t k = sh * shard_cap + j;
+        const uint64_t dst = s.soff[s.rb[k]] + s.rs[k];
+        if (dst >= s.ocap) continue;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            s.ox[(size_t)w * s.ocap + dst] = s.rx[(size_t)w * s.rcap + k];
+            s.oz[(size_t)w * s.ocap + dst] = s.rz[(size_t)w * s.rcap + k];
+        }
+        oc[dst] = rc[k];
+    }
+}
+
 template <int W, typename T>
 __global__ void k_spill_move(const uint64_t* rx, const uint64_t* rz, const T* rc, const uint32_t* rb,
                              const uint32_t* rs, uint64_t rcap, const unsigned long long* shard_fill,

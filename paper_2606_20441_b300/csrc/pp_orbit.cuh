@@ -557,12 +557,14 @@ __device__ bool orbit_bucket(const OrbTile<W, T>& t, const OrbCaps& K, const Act
 }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(32 * ORB_WARPS) k_process_orbit(StepParams p, OrbCaps K) {
+__global__ void __launch_bounds__(32 * ORB_WARPS) k_process_orbit(const StepParams p0, const StepParams* ps, OrbCaps K) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T s_cs[64 * W], s_sn[64 * W];
     __shared__ uint8_t s_ltab[16];
     __shared__ unsigned long long s_acc[3];
     __shared__ ActDesc s_ad, s_adn;
+    __shared__ StepParams p;
+    if (!load_params(p, p0, ps)) return;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SubLayerDesc& d = *p.desc;
     if (threadIdx.x < 3) s_acc[threadIdx.x] = 0ull;
