@@ -67,7 +67,11 @@ typedef struct {
     int precision;                 /* PP_PRECISION_FP64 (default) or PP_PRECISION_FP32:
                                       storage and branching type of coefficients; noise
                                       exponents and the final sum are always exact or FP64 */
-    size_t max_terms;              /* live-term capacity per buffer; 0 = derive from free memory */
+    size_t max_terms;              /* largest live-term capacity per buffer; 0 = a quarter of
+                                      the free device memory (re-read at each growth).  The
+                                      buffers start at 2^16 terms (or 4x the observable) and
+                                      grow during a propagation when a sub-layer's planned
+                                      output would need more (pp_stats.growths, .capacity) */
     void* (*alloc)(size_t bytes, void* ctx);   /* device allocator; NULL = cudaMalloc */
     void (*free)(void* ptr, void* ctx);        /* matching release; NULL = cudaFree   */
     void* alloc_ctx;
@@ -116,10 +120,14 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
  *   w_max  Pauli-weight cap (< 0: none)
  * The host waits for the device once per fused sub-layer (to size the next
  * sub-layer's buckets from the live-term count); the tiers of a sub-layer and
- * the overflow grouping run back to back on the device.
+ * the overflow grouping run back to back on the device.  Before a sub-layer
+ * whose planned output would fill more than half the buffers, and after one
+ * whose output did not fit, the buffers grow (up to the capacity limit) and
+ * the sub-layer runs (again) from its unchanged input.
  * Synchronises the handle's stream.  Errors: PP_ERR_STATE (no circuit),
- * PP_ERR_ARG, PP_ERR_NOMEM, PP_ERR_CAPACITY (more live terms than the capacity;
- * raise pp_options.max_terms), PP_ERR_CUDA. */
+ * PP_ERR_ARG, PP_ERR_NOMEM (a buffer, or a growth, could not be allocated; the
+ * handle stays usable), PP_ERR_CAPACITY (more live terms than the capacity
+ * limit; raise pp_options.max_terms), PP_ERR_TIMEOUT (pp_cancel), PP_ERR_CUDA. */
 pp_status pp_propagate(pp_handle* h, size_t n_terms, const uint64_t* ox, const uint64_t* oz,
                        const double* oc, double eps, int w_max);
 
@@ -211,8 +219,10 @@ typedef struct {
     double bytes_per_string;  /* bytes of one stored string (x, z words and coefficient) */
     int orbit_launches;       /* tier-0 launches that used the orbit tiles (the rest of
                                  tier 0 used the sparse warp tiles)                      */
-    int retries;              /* sub-layers run twice because their output outgrew the
-                                 planned buckets and the overflow area                   */
+    int retries;              /* sub-layer runs repeated because their output outgrew
+                                 the planned buckets, the overflow area or the capacity  */
+    int growths;              /* capacity growths during the propagation                 */
+    size_t capacity;          /* terms per arena at the end of the propagation           */
 } pp_stats;
 
 pp_status pp_get_stats(const pp_handle* h, pp_stats* out);

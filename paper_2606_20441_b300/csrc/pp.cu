@@ -48,6 +48,8 @@ constexpr TierCfg kTiers[N_TIERS] = {
 constexpr int kGlobalTier = N_TIERS - 1;
 constexpr int kFallbackCTAs = 16; // CTAs of the global tier
 constexpr int kFallbackCap = 1 << 20;
+constexpr size_t kMinCap = 4096;        // smallest capacity (terms per arena)
+constexpr size_t kInitialCap = 1 << 16;  // first capacity of a handle without a fixed one
 
 struct NoiseHost {
     int mode = 0;
@@ -127,6 +129,7 @@ struct pp_handle {
     std::vector<void*> owned;
 
     bool mem_ready = false;        // every work buffer below is allocated
+    int growths = 0;               // capacity growths of the running propagation
     std::atomic<long long> run_gen{0};       // generation of the running (or last) propagation
     std::atomic<long long> cancel_gen{-1};   // generation pp_cancel asked to stop
 
@@ -498,18 +501,6 @@ size_t global_slice_bytes(const pp_handle* h, int cap) {
     return (carved + 255) & ~(size_t)255;
 }
 
-// The global tier's tiles: kFallbackCTAs slices, each for up to a quarter of
-// the handle's capacity (at most kFallbackCap strings), allocated the first
-// time a bucket reaches that tier.
-pp_status ensure_global_tier(pp_handle* h) {
-    if (h->fb_scratch) return PP_OK;
-    h->fb_cap = (int)std::min<size_t>(kFallbackCap, std::max<size_t>(4096, h->cap / 4));
-    h->fb_slice = global_slice_bytes(h, h->fb_cap);
-    h->fb_scratch = static_cast<unsigned char*>(dev_alloc(h, h->fb_slice * kFallbackCTAs));
-    if (!h->fb_scratch) return fail(h, PP_ERR_NOMEM, "global-tier scratch allocation failed");
-    return PP_OK;
-}
-
 pp_status alloc_arena(pp_handle* h, Arena* a, size_t cap) {
     a->x = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
     a->z = static_cast<uint64_t*>(dev_alloc(h, cap * 8 * h->W));
@@ -518,30 +509,122 @@ pp_status alloc_arena(pp_handle* h, Arena* a, size_t cap) {
     return PP_OK;
 }
 
+// The capacity-dependent work buffers: two term arenas, the raw and grouped
+// overflow areas (a quarter of an arena each), bucket fill counters and
+// overflow offsets, the tiers' work lists and the global tier's tiles.  They
+// grow with the propagation (grow_capacity).  The other work buffers
+// (counters, partial sums, top-K state) have fixed sizes.
+struct CapMem {
+    size_t cap = 0, spill_cap = 0;
+    uint32_t fill_cap = 0;
+    Arena arena[2], spill_raw, spill_grp;
+    uint32_t* spill_b = nullptr;
+    uint32_t* spill_s = nullptr;
+    uint32_t* fill[2] = {nullptr, nullptr};
+    uint64_t* soff[2] = {nullptr, nullptr};
+    uint32_t* pass_list[N_TIERS - 1] = {nullptr, nullptr, nullptr};
+    unsigned char* fb_scratch = nullptr;
+    size_t fb_slice = 0;
+    int fb_cap = 0;
+};
+
+void put_cap_memory(pp_handle* h, const CapMem& m) {
+    h->cap = m.cap;
+    h->spill_cap = m.spill_cap;
+    h->fill_cap = m.fill_cap;
+    for (int s = 0; s < 2; ++s) {
+        h->arena[s] = m.arena[s];
+        h->fill[s] = m.fill[s];
+        h->soff[s] = m.soff[s];
+    }
+    h->spill_raw = m.spill_raw;
+    h->spill_grp = m.spill_grp;
+    h->spill_b = m.spill_b;
+    h->spill_s = m.spill_s;
+    for (int k = 0; k < N_TIERS - 1; ++k) h->pass_list[k] = m.pass_list[k];
+    h->fb_scratch = m.fb_scratch;
+    h->fb_slice = m.fb_slice;
+    h->fb_cap = m.fb_cap;
+}
+
+// Moves the capacity-dependent buffers out of the handle, which then holds none.
+CapMem take_cap_memory(pp_handle* h) {
+    CapMem m;
+    m.cap = h->cap;
+    m.spill_cap = h->spill_cap;
+    m.fill_cap = h->fill_cap;
+    for (int s = 0; s < 2; ++s) {
+        m.arena[s] = h->arena[s];
+        m.fill[s] = h->fill[s];
+        m.soff[s] = h->soff[s];
+    }
+    m.spill_raw = h->spill_raw;
+    m.spill_grp = h->spill_grp;
+    m.spill_b = h->spill_b;
+    m.spill_s = h->spill_s;
+    for (int k = 0; k < N_TIERS - 1; ++k) m.pass_list[k] = h->pass_list[k];
+    m.fb_scratch = h->fb_scratch;
+    m.fb_slice = h->fb_slice;
+    m.fb_cap = h->fb_cap;
+    put_cap_memory(h, CapMem());
+    return m;
+}
+
+void free_cap_memory(pp_handle* h, CapMem& m) {
+    for (Arena* a : {&m.arena[0], &m.arena[1], &m.spill_raw, &m.spill_grp})
+        for (void* q : {(void*)a->x, (void*)a->z, a->c}) dev_free(h, q);
+    for (void* q : {(void*)m.spill_b, (void*)m.spill_s, (void*)m.fill[0], (void*)m.fill[1], (void*)m.soff[0],
+                    (void*)m.soff[1], (void*)m.pass_list[0], (void*)m.pass_list[1], (void*)m.pass_list[2],
+                    (void*)m.fb_scratch})
+        dev_free(h, q);
+    m = CapMem();
+}
+
+// Allocates the capacity-dependent buffers for `cap` terms into the handle
+// (which holds none).  On failure the caller releases what was made.
+pp_status alloc_cap_memory(pp_handle* h, size_t cap) {
+    h->cap = cap;
+    pp_status st;
+    for (int s = 0; s < 2; ++s)
+        if ((st = alloc_arena(h, &h->arena[s], cap)) != PP_OK) return st;
+    h->spill_cap = std::max<size_t>(cap / 4, 4096) / NSPILL * NSPILL;
+    if ((st = alloc_arena(h, &h->spill_raw, h->spill_cap)) != PP_OK) return st;
+    if ((st = alloc_arena(h, &h->spill_grp, h->spill_cap)) != PP_OK) return st;
+    h->spill_b = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
+    h->spill_s = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
+    if (!h->spill_b || !h->spill_s) return fail(h, PP_ERR_NOMEM, "overflow index allocation failed");
+    // up to one bucket per 16 terms of capacity
+    h->fill_cap = (uint32_t)std::min<size_t>(std::max<size_t>(cap / 16, 1024), 1u << 28);
+    for (int s = 0; s < 2; ++s) {
+        h->fill[s] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
+        h->soff[s] = static_cast<uint64_t*>(dev_alloc(h, sizeof(uint64_t) * h->fill_cap));
+        if (!h->fill[s] || !h->soff[s]) return fail(h, PP_ERR_NOMEM, "bucket counters allocation failed");
+    }
+    for (int k = 0; k < N_TIERS - 1; ++k)
+        if (!(h->pass_list[k] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap))))
+            return fail(h, PP_ERR_NOMEM, "work lists allocation failed");
+    // the global tier: kFallbackCTAs tiles of up to a quarter of the capacity
+    // (at most kFallbackCap strings)
+    h->fb_cap = (int)std::min<size_t>(kFallbackCap, std::max<size_t>(4096, cap / 4));
+    h->fb_slice = global_slice_bytes(h, h->fb_cap);
+    h->fb_scratch = static_cast<unsigned char*>(dev_alloc(h, h->fb_slice * kFallbackCTAs));
+    if (!h->fb_scratch) return fail(h, PP_ERR_NOMEM, "global-tier scratch allocation failed");
+    return PP_OK;
+}
+
 // Releases every work buffer of the handle (not its table arena) and resets
 // the pointers, so that a failed set-up leaves the handle as it was created.
 void release_work_memory(pp_handle* h) {
+    CapMem m = take_cap_memory(h);
+    free_cap_memory(h, m);
     auto rel = [&](auto*& ptr) {
         if (ptr) dev_free(h, (void*)ptr);
         ptr = nullptr;
     };
-    for (Arena* a : {&h->arena[0], &h->arena[1], &h->spill_raw, &h->spill_grp}) {
-        rel(a->x);
-        rel(a->z);
-        rel(a->c);
-    }
-    rel(h->spill_b);
-    rel(h->spill_s);
     rel(h->spill_ctr);
-    for (int s = 0; s < 2; ++s) {
-        rel(h->fill[s]);
-        rel(h->soff[s]);
-    }
     rel(h->counters);
-    for (auto& l : h->pass_list) rel(l);
     rel(h->partial);
     rel(h->topk_state);
-    rel(h->fb_scratch);
     rel(h->stage);
     rel(h->sort_scratch);
     h->stage_cap = 0;
@@ -549,14 +632,35 @@ void release_work_memory(pp_handle* h) {
     h->mem_ready = false;
 }
 
-pp_status ensure_memory_once(pp_handle* h);
+// Largest capacity the handle may grow to: pp_options.max_terms, or, when
+// that is 0, a quarter of the device memory that is free or already held by
+// this handle's arenas per arena (two arenas and two quarter-arena overflow
+// areas: ~62% of it).
+size_t cap_limit(pp_handle* h) {
+    if (h->opt.max_terms) return std::max<size_t>(h->opt.max_terms, kMinCap);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return std::max<size_t>(h->cap, kMinCap);
+    }
+    const double held = 2.5 * (double)h->cap * (double)term_bytes(h);
+    return std::max<size_t>(kMinCap, (size_t)(0.25 * ((double)fr + held) / (double)term_bytes(h)));
+}
 
-// Work buffers, allocated at the first propagation.  All or nothing: when an
-// allocation fails, the ones made so far are released and PP_ERR_NOMEM is
-// returned with the handle unchanged, so a later call can try again.
-pp_status ensure_memory(pp_handle* h) {
+// Work buffers, allocated at the first propagation with room for `want`
+// terms (at most the capacity limit).  All or nothing: when an allocation
+// fails, the ones made so far are released and PP_ERR_NOMEM is returned with
+// the handle unchanged, so a later call can try again.
+pp_status ensure_memory(pp_handle* h, size_t want) {
     if (h->mem_ready) return PP_OK;
-    pp_status st = ensure_memory_once(h);
+    pp_status st = PP_OK;
+    h->spill_ctr = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * NSPILL));
+    h->counters = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * CTR_COUNT));
+    h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * (4096 + 1)));
+    h->topk_state = static_cast<TopKState*>(dev_alloc(h, sizeof(TopKState)));
+    if (!h->spill_ctr || !h->counters || !h->partial || !h->topk_state)
+        st = fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
+    if (st == PP_OK) st = alloc_cap_memory(h, std::max(kMinCap, std::min(want, cap_limit(h))));
     if (st != PP_OK) {
         cudaStreamSynchronize(h->st);
         std::string msg = h->err;
@@ -568,43 +672,52 @@ pp_status ensure_memory(pp_handle* h) {
     return PP_OK;
 }
 
-pp_status ensure_memory_once(pp_handle* h) {
-    size_t tb = term_bytes(h);
-    size_t cap = h->opt.max_terms;
-    if (cap == 0) {
-        size_t fr = 0, tot = 0;
-        CK(cudaMemGetInfo(&fr, &tot));
-        // two term arenas and two overflow areas of a quarter arena: ~62% of free memory
-        cap = (size_t)(0.25 * (double)fr) / tb;
+// Grows the capacity to `want` terms (bounded by the limit; nothing happens
+// when that is no gain), keeping the layout the next sub-layer reads: `B`
+// bucket regions of `C` terms on arena `side`, their fill counters and
+// overflow offsets, and `n_over` grouped overflow terms.  Word w of a term
+// array starts at w * capacity, so each word's used prefix is copied to the
+// same index in the larger array; the layout's region size stays C.  On
+// PP_ERR_NOMEM the handle keeps its old buffers and layout.
+pp_status grow_capacity(pp_handle* h, size_t want, int side, uint32_t B, uint64_t C, uint64_t n_over) {
+    const size_t cap = std::min(want, cap_limit(h));
+    if (cap <= h->cap) return PP_OK;
+    CapMem old = take_cap_memory(h);
+    pp_status st = alloc_cap_memory(h, cap);
+    if (st != PP_OK) {
+        std::string msg = h->err;
+        CapMem part = take_cap_memory(h);
+        free_cap_memory(h, part);
+        put_cap_memory(h, old);
+        h->err = msg;
+        return st;
     }
-    cap = std::max<size_t>(cap, 4096);
-    h->cap = cap;
-    pp_status st;
-    for (int s = 0; s < 2; ++s)
-        if ((st = alloc_arena(h, &h->arena[s], cap)) != PP_OK) return st;
-    h->spill_cap = std::max<size_t>(cap / 4, 4096) / NSPILL * NSPILL;
-    if ((st = alloc_arena(h, &h->spill_raw, h->spill_cap)) != PP_OK) return st;
-    if ((st = alloc_arena(h, &h->spill_grp, h->spill_cap)) != PP_OK) return st;
-    h->spill_b = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
-    h->spill_s = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->spill_cap));
-    h->spill_ctr = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * NSPILL));
-    if (!h->spill_ctr) return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
-    h->fill_cap = (uint32_t)std::min<size_t>(std::max<size_t>(cap / 64, 1024), 1u << 28);
-    for (int s = 0; s < 2; ++s) {
-        h->fill[s] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap));
-        h->soff[s] = static_cast<uint64_t*>(dev_alloc(h, sizeof(uint64_t) * h->fill_cap));
-        if (!h->fill[s] || !h->soff[s]) return fail(h, PP_ERR_NOMEM, "bucket counters allocation failed");
+    const size_t cb = h->opt.precision == PP_PRECISION_FP32 ? 4 : 8;
+    const size_t n_reg = std::min<size_t>((size_t)B * C, old.cap);
+    const size_t n_ov = std::min<size_t>(n_over, old.spill_cap);
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->st);
+    };
+    for (int w = 0; w < h->W; ++w) {
+        cp(h->arena[side].x + (size_t)w * h->cap, old.arena[side].x + (size_t)w * old.cap, n_reg * 8);
+        cp(h->arena[side].z + (size_t)w * h->cap, old.arena[side].z + (size_t)w * old.cap, n_reg * 8);
+        cp(h->spill_grp.x + (size_t)w * h->spill_cap, old.spill_grp.x + (size_t)w * old.spill_cap, n_ov * 8);
+        cp(h->spill_grp.z + (size_t)w * h->spill_cap, old.spill_grp.z + (size_t)w * old.spill_cap, n_ov * 8);
     }
-    h->counters = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long) * CTR_COUNT));
-    for (int k = 0; k < N_TIERS - 1; ++k)
-        if (!(h->pass_list[k] = static_cast<uint32_t*>(dev_alloc(h, sizeof(uint32_t) * h->fill_cap))))
-            return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
-    h->partial = static_cast<__int128*>(dev_alloc(h, sizeof(__int128) * (4096 + 1)));
-    h->topk_state = static_cast<TopKState*>(dev_alloc(h, sizeof(TopKState)));
-    if (!h->topk_state) return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
-    if (!h->spill_b || !h->spill_s || !h->counters || !h->partial)
-        return fail(h, PP_ERR_NOMEM, "work buffers allocation failed");
-    return ensure_global_tier(h);
+    cp(h->arena[side].c, old.arena[side].c, n_reg * cb);
+    cp(h->spill_grp.c, old.spill_grp.c, n_ov * cb);
+    cp(h->fill[side], old.fill[side], sizeof(uint32_t) * B);
+    cp(h->soff[side], old.soff[side], sizeof(uint64_t) * B);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    else cudaStreamSynchronize(h->st);
+    free_cap_memory(h, old);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, PP_ERR_CUDA, "capacity growth copy failed: %s", cudaGetErrorString(e));
+    }
+    h->growths++;
+    return PP_OK;
 }
 
 // Smallest power of two >= v, but at most the largest power of two <= cap.
@@ -1032,6 +1145,25 @@ struct Prop {
             return fail(h, PP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
     } while (0)
 
+// The launch parameters that point into the capacity-dependent buffers
+// (they move when the capacity grows).
+void set_capacity_params(Prop& P) {
+    pp_handle* h = P.h;
+    StepParams& p = P.p;
+    p.rpx = h->spill_raw.x;
+    p.rpz = h->spill_raw.z;
+    p.rpc = h->spill_raw.c;
+    p.rpb = h->spill_b;
+    p.rps = h->spill_s;
+    p.rpcap = h->spill_cap;
+    p.spx = h->spill_grp.x;
+    p.spz = h->spill_grp.z;
+    p.spc = h->spill_grp.c;
+    p.spcap = h->spill_cap;
+    p.gcap = h->fb_cap;
+    p.gslice = h->fb_slice;
+}
+
 // Validates, plans, stages the observable and scatters it into the first
 // sub-layer's buckets (one synchronisation).
 pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, const uint64_t* oz,
@@ -1048,7 +1180,10 @@ pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, 
     P.gen = ++h->run_gen;
     pp_status st;
     if (h->subs_dirty && (st = build_plan(h)) != PP_OK) return st;
-    if ((st = ensure_memory(h)) != PP_OK) return st;
+    h->growths = 0;
+    const size_t want = std::max<size_t>(kInitialCap, 4 * n_terms);
+    if ((st = ensure_memory(h, want)) != PP_OK) return st;
+    if (2 * n_terms > h->cap && (st = grow_capacity(h, want, 0, 0, 0, 0)) != PP_OK) return st;
     if (!P.ctr_dev) P.ctr_dev = h->counters;
     const int W = h->W;
 
@@ -1082,20 +1217,9 @@ pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, 
     p.eps_f = eps_float_ceil(eps);
     p.w_max = w_max;
     p.counters = P.ctr_dev;
-    p.rpx = h->spill_raw.x;
-    p.rpz = h->spill_raw.z;
-    p.rpc = h->spill_raw.c;
-    p.rpb = h->spill_b;
-    p.rps = h->spill_s;
-    p.rpcap = h->spill_cap;
     p.spill_ctr = h->spill_ctr;
-    p.spx = h->spill_grp.x;
-    p.spz = h->spill_grp.z;
-    p.spc = h->spill_grp.c;
-    p.spcap = h->spill_cap;
     p.phase = P.trace ? P.ctr_dev + CTR_PHASE : nullptr;
-    p.gcap = h->fb_cap;
-    p.gslice = h->fb_slice;
+    set_capacity_params(P);
 
     // scatter the input into the first sub-layer's buckets
     P.side = 0;
@@ -1132,10 +1256,17 @@ pp_status prop_setup(Prop& P) {
     const SubLayerDesc& d = h->subs[P.s];
     const bool fin = d.final_ != 0;
     if (P.attempt == 0) {
-        const double est = std::max(64.0, (double)P.N * P.growth_of(P.s) * 1.3);
+        const double out = (double)P.N * P.growth_of(P.s);   // expected output
+        // grow first when the output would fill more than half the buffers
+        if (2.0 * out > (double)h->cap) {
+            pp_status st = grow_capacity(h, (size_t)(2.5 * out), P.side, P.B, P.C, P.n_over_in);
+            if (st != PP_OK) return st;
+        }
+        const double est = std::max(64.0, out * 1.3);
         P.nB = fin ? 1 : P.buckets_for(P.s + 1, est);
         P.nC = fin ? h->cap : h->cap / P.nB;
     }
+    set_capacity_params(P);
     StepParams& p = P.p;
     p.sx = h->arena[P.side].x;
     p.sz = h->arena[P.side].z;
@@ -1209,20 +1340,30 @@ pp_status prop_finish(Prop& P) {
     P.stats.fallback_buckets += (int)passed[kGlobalTier - 1];
     if (ctr[CTR_ERR_FALLBACK])
         return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s, h->fb_cap);
-    // A sub-layer whose output outgrew the planned buckets and the overflow area
-    // runs once more with buckets sized from its true output count: its source
-    // layout is only read, and its noise map (applied in place) is not applied again.
-    if (ctr[CTR_ERR_REGION] && !fin && P.attempt == 0 && ctr[CTR_OUT] <= h->cap) {
-        P.growth[h->sub_kind[s]] = std::max(0.05, (double)ctr[CTR_OUT] / std::max<double>(1.0, (double)P.N));
-        P.nB = P.buckets_for(s + 1, std::max(64.0, 1.3 * (double)ctr[CTR_OUT]));
-        P.nC = h->cap / P.nB;
-        P.stats.retries++;
-        P.attempt = 1;
-        return PP_OK;
+    // A sub-layer whose output outgrew the planned buckets, the overflow area or
+    // the capacity runs again (at most twice more), after the capacity has
+    // grown to twice its true output, with buckets sized from that output: its
+    // source layout is only read, and its noise map (applied in place) is not
+    // applied again.
+    const double out = (double)ctr[CTR_OUT];
+    if ((ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap) && P.attempt < 2) {
+        P.growth[h->sub_kind[s]] = std::max(0.05, out / std::max<double>(1.0, (double)P.N));
+        if (2.0 * out > (double)h->cap) {
+            pp_status st = grow_capacity(h, (size_t)(2.0 * out), P.side, P.B, P.C, P.n_over_in);
+            if (st != PP_OK) return st;
+        }
+        if (out <= (double)h->cap) {
+            P.nB = fin ? 1 : P.buckets_for(s + 1, std::max(64.0, 1.3 * out));
+            P.nC = fin ? h->cap : h->cap / P.nB;
+            P.stats.retries++;
+            P.attempt++;
+            return PP_OK;
+        }
     }
     if (ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap)
         return fail(h, PP_ERR_CAPACITY, "sub-layer %d: %llu live terms exceed the capacity (%zu terms, "
-                    "%zu overflow); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap, h->spill_cap);
+                    "%zu overflow; limit %zu); raise max_terms", s, (unsigned long long)ctr[CTR_OUT], h->cap,
+                    h->spill_cap, cap_limit(h));
     const unsigned long long n_spill_out = fin ? 0ull : ctr[CTR_SPILL_TOTAL];
     // canonical gate-by-gate count (live terms entering each gate in listed
     // order), summed by the kernels over string lifetimes
@@ -1279,6 +1420,8 @@ void prop_end(Prop& P) {
     P.stats.updates = P.updates;
     P.stats.kernel_launches = P.launches;
     P.stats.bytes_per_string = (double)term_bytes(h);
+    P.stats.growths = h->growths;
+    P.stats.capacity = h->cap;
     P.stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - P.t0).count();
     h->stats = P.stats;
     P.finished = true;

@@ -54,7 +54,9 @@ class pp_stats(ctypes.Structure):
                 ("tier_strings", ctypes.c_double * 4),
                 ("bytes_per_string", ctypes.c_double),
                 ("orbit_launches", ctypes.c_int),
-                ("retries", ctypes.c_int)]
+                ("retries", ctypes.c_int),
+                ("growths", ctypes.c_int),
+                ("capacity", ctypes.c_size_t)]
 
 
 class pp_batch_item(ctypes.Structure):

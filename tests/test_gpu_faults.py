@@ -121,3 +121,67 @@ def test_cancel_after_finish_has_no_effect(pp):
         assert h.pp_expect() == e1
     finally:
         h.close()
+
+
+def test_capacity_grows_during_a_propagation(pp):
+    """A handle starts with small buffers and grows them when a sub-layer's
+    output needs more; the result is the oracle's."""
+    inst = inputs.workload_6x6(steps=4, eps=1e-4)      # peak 1.8e5 terms
+    ref = oracle.run(inst)
+    h = pp.Handle(inst.n_qubits)
+    try:
+        h.load_instance(inst)
+        h.run_instance(inst)
+        st = h.pp_get_stats()
+        assert st.growths >= 1 and st.capacity >= st.peak_terms > (1 << 16)
+        compare_terms(h.pp_export_terms(), (ref.x, ref.z, ref.c), inst.eps)
+        assert abs(h.pp_expect() - ref.expect) <= 1e-12
+        h.run_instance(inst)                    # already large enough: no growth
+        assert h.pp_get_stats().growths == 0
+        compare_terms(h.pp_export_terms(), (ref.x, ref.z, ref.c), inst.eps)
+    finally:
+        h.close()
+
+
+def test_capacity_limit_reports_capacity(pp):
+    inst = inputs.workload_6x6(steps=3, eps=1e-4)
+    h = pp.Handle(inst.n_qubits, max_terms=10_000)     # the peak is 2.2e4 terms
+    try:
+        h.load_instance(inst)
+        with pytest.raises(pp.PPError) as ei:
+            h.run_instance(inst)
+        assert ei.value.status == pp.PP_ERR_CAPACITY
+        small = inputs.workload_6x6(steps=1, eps=1e-3)
+        ref = oracle.run(small)
+        h.load_instance(small)
+        h.run_instance(small)
+        compare_terms(h.pp_export_terms(), (ref.x, ref.z, ref.c), small.eps)
+    finally:
+        h.close()
+
+
+def test_refused_growth_reports_nomem_and_recovers(pp):
+    """The allocator refuses once the first propagation's buffers exist: the
+    next propagation, which must grow them, ends with PP_ERR_NOMEM; the handle
+    keeps its buffers and, once memory is given again, matches the oracle."""
+    tiny = inputs.workload_6x6(steps=1, eps=1e-2)
+    inst = inputs.workload_6x6(steps=4, eps=1e-4)
+    ref = oracle.run(inst)
+    a = RefusingAllocator(None)
+    h = pp.Handle(inst.n_qubits, allocator=(a.alloc, a.free))
+    try:
+        h.load_instance(tiny)
+        h.run_instance(tiny)
+        assert h.pp_get_stats().growths == 0
+        h.load_instance(inst)
+        a.budget = a.calls + 1                   # e.g. the circuit tables, not a growth
+        with pytest.raises(pp.PPError) as ei:
+            h.run_instance(inst)
+        assert ei.value.status == pp.PP_ERR_NOMEM and a.refused > 0
+        a.budget = None
+        h.run_instance(inst)
+        assert h.pp_get_stats().growths >= 1
+        compare_terms(h.pp_export_terms(), (ref.x, ref.z, ref.c), inst.eps)
+    finally:
+        h.close()
+    assert not a.live
