@@ -40,10 +40,16 @@ struct TierCfg {
     int cap1;     // tile entries for W = 1
     int cap2;     // tile entries for W = 2
 };
+#ifndef PP_TIER1_THREADS
+#define PP_TIER1_THREADS 64
+#endif
+#ifndef PP_TIER2_THREADS
+#define PP_TIER2_THREADS 256
+#endif
 constexpr TierCfg kTiers[N_TIERS] = {
     {32 * WARP_TILE_WARPS, 248, 248},   // one warp per bucket
-    {64, 1024, 1024},                   // CTA tiles: few warps, so that a round's
-    {256, 4096, 2048},                  // barriers wait on few warps
+    {PP_TIER1_THREADS, 1024, 1024},     // CTA tiles: few warps, so that a round's
+    {PP_TIER2_THREADS, 4096, 2048},     // barriers wait on few warps
     {512, 1 << 20, 1 << 20}};           // global-memory tile
 constexpr int kGlobalTier = N_TIERS - 1;
 constexpr int kFallbackCTAs = 16; // CTAs of the global tier
@@ -268,6 +274,15 @@ double bucket_headroom(const pp_handle* h) {
 void set_orbit_table(SubLayerDesc& d) {
     d.orb = (d.cls == CLS_NONE) || ((d.cls == CLS_LOCAL1 || d.cls == CLS_LOCAL2) && d.nseg == 1);
     std::memset(d.ltab, 0xff, sizeof(d.ltab));
+    // listed index == slot: generic sub-layers, and class sub-layers whose
+    // slots form one ascending run 0, 1, ..., n_gates - 1
+    d.ident = d.cls == CLS_GENERIC || d.cls == CLS_NONE;
+    if ((d.cls == CLS_LOCAL1 || d.cls == CLS_LOCAL2) && d.nseg == 1) {
+        bool ok = true;
+        for (int g = 0; g < d.n_gates && ok; ++g) ok = d.slot_of[g] == g;
+        d.ident = ok;
+    }
+    d.psign = 0;
     if (d.cls != CLS_LOCAL1 && d.cls != CLS_LOCAL2) return;
     const int two = d.cls == CLS_LOCAL2;
     const int ra = d.ax + 2 * d.az, rb = two ? d.bx + 2 * d.bz : 0;
@@ -278,6 +293,13 @@ void set_orbit_table(SubLayerDesc& d) {
         const int rx = r & 1, rz = r >> 1, sx = s & 1, sz = s >> 1;
         return rx * rz + sx * sz + 2 * rz * sx - ((rx ^ sx) & (rz ^ sz));
     };
+    // the sign of any acting string's sin-branch, by its letters on the sites
+    for (int la = 0; la < 4; ++la)
+        for (int lb = 0; lb < (two ? 4 : 1); ++lb) {
+            if (!(anti(la, ra) ^ anti(lb, rb))) continue;
+            const int e = (ph(ra, la) + (two ? ph(rb, lb) : 0)) & 3;
+            if (((1 + e) & 3) != 0) d.psign |= (uint16_t)(1u << (la + 4 * lb));
+        }
     for (int la = 0; la < 4; ++la)
         for (int lb = 0; lb < (two ? 4 : 1); ++lb) {
             const int cbit = d.ax ? (la & 1) : (la >> 1);
@@ -1389,14 +1411,16 @@ pp_status prop_finish(Prop& P) {
                 "\"spill\": %llu, \"ms\": [%.4f, %.4f, %.4f, %.4f], "
                 "\"tier_strings\": [%llu, %llu, %llu, %llu], "
                 "\"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
-                "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu]}\n",
+                "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu], "
+                "\"t0_stat\": [%llu, %llu, %llu, %llu, %llu, %llu, %llu]}\n",
                 s, d.cls, d.n_gates, (int)P.use_orbit(s), P.N, Nout, P.B, P.nB, passed[0], passed[1], passed[2],
                 n_spill_out, P.ms[0], P.ms[1], P.ms[2], P.ms[3],
                 ctr[CTR_LOADED] + ctr[CTR_EMITTED], ctr[CTR_LOADED + 1] + ctr[CTR_EMITTED + 1],
                 ctr[CTR_LOADED + 2] + ctr[CTR_EMITTED + 2], ctr[CTR_LOADED + 3] + ctr[CTR_EMITTED + 3],
                 ctr[CTR_FAIL], ctr[CTR_FAIL + 1], ctr[CTR_FAIL + 2], ctr[CTR_PHASE], ctr[CTR_PHASE + 1],
                 ctr[CTR_PHASE + 2], ctr[CTR_PHASE + 3], ctr[CTR_PHASE_CTA], ctr[CTR_PHASE_CTA + 1],
-                ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3]);
+                ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3], ctr[CTR_STAT], ctr[CTR_STAT + 1],
+                ctr[CTR_STAT + 2], ctr[CTR_STAT + 3], ctr[CTR_STAT + 4], ctr[CTR_STAT + 5], ctr[CTR_STAT + 6]);
     if (P.N > 0) P.growth[h->sub_kind[s]] = std::max(0.05, (double)Nout / (double)P.N);
     P.N = Nout;
     P.n_over_in = n_spill_out;

@@ -51,6 +51,12 @@ struct SubLayerDesc {
     int first;                    // 1: input observable (merge duplicates, truncate)
     int final_;                   // 1: last sub-layer (outputs go to the compact result)
     int layer_end;                // 1: last sub-layer of a circuit layer (top-K applies after it)
+    int ident;                    // 1: a gate's listed index equals its slot (one ascending
+                                  //    segment starting at slot 0 with no gaps, or generic)
+    uint16_t psign;               // class sub-layers: bit la + 4 lb set when a string with
+                                  //    letters (la, lb) (code x + 2z) on a gate's sites
+                                  //    (a, a + shift) sends its sin-branch into its partner
+                                  //    with a negative sign (i R P = -P')
     int orb;                      // 1: one letter pattern, one ascending segment, disjoint
                                   //    supports: the orbit tier may process it (pp_orbit.cuh)
     // Orbit sub-layers: for the letters (la, lb) (code x + 2z) that the member
@@ -76,7 +82,7 @@ struct ActDesc {
     int ax, az, bx, bz;
     int shift;
     int n_gates;
-    int pad_;
+    int ident;                    // SubLayerDesc::ident
     uint64_t all[MAXW];
     int16_t order[MAX_SITES];
     const uint64_t* gx;           // generic generators [MAX_GEN][MAXW], in global memory
@@ -224,6 +230,7 @@ __device__ __forceinline__ void make_act(const SubLayerDesc& s, ActDesc& d) {
     d.ax = s.ax; d.az = s.az; d.bx = s.bx; d.bz = s.bz;
     d.shift = s.shift;
     d.n_gates = s.n_gates;
+    d.ident = s.ident;
     for (int w = 0; w < MAXW; ++w) d.all[w] = s.all[w];
     for (int i = 0; i < MAX_SITES; ++i) d.order[i] = s.order[i];
     d.gx = &s.gx[0][0];

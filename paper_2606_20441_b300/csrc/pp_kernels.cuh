@@ -80,7 +80,9 @@ enum {
     CTR_PHASE = 28,      // tier-0 cycles per phase when tracing (28..31)
     CTR_PHASE_CTA = 32,  // CTA-tier cycles per phase when tracing (32..35)
     CTR_UPDATES = 36,    // canonical work count of the completed buckets (string lifetimes)
-    CTR_COUNT = 37
+    CTR_STAT = 37,       // tier-0 work statistics when tracing (37..44): buckets, rounds,
+                         // list chunks, listed strings, live pairs, created, revived, 0
+    CTR_COUNT = 45
 };
 
 // Number of work items (buckets) of a tier launch.
@@ -127,9 +129,10 @@ struct Tile {
     uint64_t* x;      // [W][cap] string
     uint64_t* z;      // [W][cap]
     uint64_t* g;      // [W][cap] gates of the sub-layer still to apply (listed-order bits)
-    T* c;             // coefficient, 0 = not live
-    T* cn;            // coefficient after the current round
-    uint8_t* gi;      // listed index of this round's gate
+    T* c;             // coefficient buffer 0 (the loaded values), 0 = not live
+    T* c1;            // coefficient buffer 1: round r reads buffer r & 1, writes the other
+    uint8_t* sr;      // stamp of the last write of each string's coefficient: 0 at
+                      // load, r + 1 in round r (the value sits in buffer stamp & 1)
     I* hash;          // [hcap] entry index or -1 (insert-only)
     I* act;           // [2][cap] strings with gates left: this round's list, the next one's
     int cap;
@@ -139,7 +142,14 @@ struct Tile {
     int* flag;        // nonzero (a FAIL_* reason): the bucket goes to the next tier
     int* live;
     int* nact;        // [2] lengths of the two active lists
+    __device__ __forceinline__ T* cbuf(int k) const { return k ? c1 : c; }
 };
+
+// Current coefficient of entry i (after the rounds: its final one).
+template <int W, typename T, typename I>
+__device__ __forceinline__ T tile_coef(const Tile<W, T, I>& t, int i) {
+    return t.cbuf(t.sr[i] & 1)[i];
+}
 
 constexpr int NWARPS = 16;    // warps per CTA of the global-memory tier (512 threads)
 
@@ -150,18 +160,69 @@ struct GateTab {
     uint64_t rz[64 * W][W];
     T cs[64 * W];
     T sn[64 * W];
+    uint8_t slot[64 * W];     // class sub-layers: first site of each gate
+    int cls;
+    int shift;
+    uint32_t psign;           // SubLayerDesc::psign
 };
 
+// Slot of a tile's hash table for key (x, z): 32-bit multiply-add of the key's
+// halves, then a multiply-xorshift finaliser.
 template <int W>
 __device__ __forceinline__ uint32_t tile_hash(const uint64_t* x, const uint64_t* z, int hbits) {
-    uint64_t h = 0;
+    uint32_t h = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w)
-        h += x[w] * (0x9E3779B97F4A7C15ULL + 2 * w) + z[w] * (0xC2B2AE3D27D4EB4FULL + 2 * w);
-    h ^= h >> 31;
-    h *= 0xD6E8FEB86659FD93ULL;
-    return (uint32_t)(h >> (64 - hbits));
+    for (int w = 0; w < W; ++w) {
+        h += (uint32_t)x[w] * (0x9E3779B1u + 4u * w) + (uint32_t)(x[w] >> 32) * (0x85EBCA77u + 4u * w);
+        h += (uint32_t)z[w] * (0xC2B2AE3Du + 4u * w) + (uint32_t)(z[w] >> 32) * (0x27D4EB2Fu + 4u * w);
+    }
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 13;
+    return h >> (32 - hbits);
 }
+
+// Letter code (x + 2z) of string (x, z) on qubit a.
+template <int W>
+__device__ __forceinline__ int letter_at(const uint64_t* x, const uint64_t* z, int a) {
+    uint64_t xw = x[0], zw = z[0];
+    if (W > 1 && a >= 64) {
+        xw = x[W - 1];
+        zw = z[W - 1];
+    }
+    const int b = a & 63;
+    return (int)((xw >> b) & 1ull) | ((int)((zw >> b) & 1ull) << 1);
+}
+
+// Whether string (x, z), acted on by listed gate gg, sends its sin-branch into
+// its partner with a negative sign: i R P = phi P' with phi = -1.  Class
+// sub-layers read it from the letters on the gate's sites; generic ones take
+// the product phase R P = i^e (R xor P).
+template <int W, typename T>
+__device__ __forceinline__ bool branch_negative(const GateTab<W, T>& tab, int gg, const uint64_t* x,
+                                                const uint64_t* z) {
+    if (tab.cls == CLS_GENERIC) {
+        const int e = product_phase<W>(tab.rx[gg], tab.rz[gg], x, z);
+        return ((1 + e) & 3) != 0;
+    }
+    const int a = tab.slot[gg];
+    int code = letter_at<W>(x, z, a);
+    if (tab.cls == CLS_LOCAL2) code |= letter_at<W>(x, z, a + tab.shift) << 2;
+    return (tab.psign >> code) & 1u;
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_coef(float* smem, const float* gmem) { cp_async4(smem, gmem); }
+__device__ __forceinline__ void cp_async_coef(double* smem, const double* gmem) { cp_async8(smem, gmem); }
 
 template <int W, typename T, typename I>
 __device__ __forceinline__ void tile_key(const Tile<W, T, I>& t, int i, uint64_t* x, uint64_t* z) {
@@ -249,20 +310,15 @@ __device__ __forceinline__ void tile_insert(const Tile<W, T, I>& t, int idx, con
 // Appends entry i to active list `which` (warp-aggregated; all lanes of the
 // warp must call it together, `want` false for lanes that append nothing).
 template <int W, typename T, typename I>
-__device__ __forceinline__ void act_append(const Tile<W, T, I>& t, int which, bool want, int i) {
+__device__ __forceinline__ void act_append(const Tile<W, T, I>& t, int which, int counter, bool want, int i) {
     const unsigned msk = __ballot_sync(0xffffffffu, want);
     if (!msk) return;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(msk) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(&t.nact[which], __popc(msk));
+    if (lane == leader) base = atomicAdd(&t.nact[counter], __popc(msk));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (want) t.act[(size_t)which * t.cap + base + __popc(msk & ((1u << lane) - 1u))] = (I)i;
-}
-
-template <typename T>
-__device__ __forceinline__ T load_coef(const void* base, size_t i) {
-    return static_cast<const T*>(base)[i];
 }
 
 template <typename T>
@@ -343,29 +399,46 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
         *t.live = 0;
         t.nact[0] = 0;
         t.nact[1] = 0;
+        t.nact[2] = 0;
     }
     __syncthreads();
     if (*t.flag) return false;
 
-    // ---- load: the bucket's region, then its overflow strings
+    // ---- load: the bucket's region, then its overflow strings (shared-memory
+    // tiles copy asynchronously, every thread's copies in flight at once), then
+    // the hash table
     const size_t base = (size_t)b * p.sC;
     const size_t obase = (n_in > p.sC) ? (size_t)p.soff[b] : 0;
+    constexpr bool kAsync = sizeof(I) == 2;   // the global tier's tile is in global memory
     for (int i = tid; i < (int)n_in; i += nt) {
-        uint64_t x[W], z[W];
         const bool reg = (uint64_t)i < p.sC;
         const size_t src = reg ? base + i : obase + (i - p.sC);
         const uint64_t* ax = reg ? p.sx : p.spx;
         const uint64_t* az = reg ? p.sz : p.spz;
         const size_t acap = reg ? p.scap : p.spcap;
+        const T* ac = static_cast<const T*>(reg ? p.sc : p.spc);
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            x[w] = ax[(size_t)w * acap + src];
-            z[w] = az[(size_t)w * acap + src];
-            t.x[(size_t)w * t.cap + i] = x[w];
-            t.z[(size_t)w * t.cap + i] = z[w];
+            if (kAsync) {
+                cp_async8(&t.x[(size_t)w * t.cap + i], &ax[(size_t)w * acap + src]);
+                cp_async8(&t.z[(size_t)w * t.cap + i], &az[(size_t)w * acap + src]);
+            } else {
+                t.x[(size_t)w * t.cap + i] = ax[(size_t)w * acap + src];
+                t.z[(size_t)w * t.cap + i] = az[(size_t)w * acap + src];
+            }
         }
-        t.c[i] = load_coef<T>(reg ? p.sc : p.spc, src);
-        if (d.first) __threadfence_block();
+        if (kAsync) cp_async_coef(&t.c[i], ac + src);
+        else t.c[i] = ac[src];
+        t.sr[i] = 0;
+    }
+    if (kAsync) {
+        cp_async_commit();
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    for (int i = tid; i < (int)n_in; i += nt) {
+        uint64_t x[W], z[W];
+        tile_key<W, T, I>(t, i, x, z);
         tile_insert<W, T, I>(t, i, x, z, d.first != 0);
     }
     __syncthreads();
@@ -396,8 +469,9 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                 ++my_live;
                 uint64_t A[W], Mx[W], Mz[W];
                 activity<W>(ad, x, z, A, Mx, Mz);
-                if (ad.cls == CLS_GENERIC) {
-                    gm[0] = A[0];
+                if (ad.ident) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) gm[w] = A[w];
                 } else {
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
@@ -416,7 +490,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
 #pragma unroll
             for (int w = 0; w < W; ++w) t.g[(size_t)w * t.cap + i] = gm[w];
         }
-        act_append<W, T, I>(t, 0, has_gates, i);
+        act_append<W, T, I>(t, 0, 0, has_gates, i);
     }
     if (my_live) atomicAdd(t.live, my_live);
     __syncthreads();
@@ -425,28 +499,36 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
 
     // ---- gate rounds.  Round r: every listed string applies the next gate of
     // its mask (orbit members share the mask, so a string and its partner use
-    // the same gate), then the next round's list keeps the strings still live
-    // with gates left.  A string's partner under its round gate is unique to
-    // it, so the lookup and the rotation share one pass; new and revived
-    // strings join the next round's list.  Counters are bumped once per warp
-    // (votes), never once per thread: in a large orbit every string applies the
-    // same gate in the same round.
+    // the same gate); the next round's list keeps the strings still live with
+    // gates left, and new and revived strings join it.  A string's partner
+    // under its round gate is unique to it, so lookup, rotation, truncation
+    // and the next list share one pass: round r reads coefficients from
+    // buffer r & 1 and writes the other, so both members of a pair read the
+    // values from before the gate.  List counters rotate over three slots
+    // (read in round r, appended in round r + 1, cleared meanwhile), so one
+    // barrier per round suffices.  Counters are bumped once per warp (votes),
+    // never once per thread: in a large orbit every string applies the same
+    // gate in the same round.
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
     for (int r = 0; r <= 64 * W; ++r) {
         const int cur = r & 1, nxt = cur ^ 1;
-        const int na = t.nact[cur];
+        const int na = t.nact[r % 3];
         if (na == 0) break;
+        if (tid == 0) t.nact[(r + 2) % 3] = 0;
         const I* L = t.act + (size_t)cur * t.cap;
+        const T* ccur = t.cbuf(cur);
+        T* cnxt = t.cbuf(nxt);
+        const uint8_t stamp = (uint8_t)(r + 1);
         for (int k0 = 0; k0 < na; k0 += nt) {
             const int k = k0 + tid;
-            bool create = false, revive = false;
-            int j = -1, gg = -1;
+            bool create = false, revive = false, keep = false;
+            int i = 0, j = -1, gg = -1;
             uint32_t hslot = 0;
             T v = T(0);
             uint64_t qx[W], qz[W], gm[W];
             if (k < na) {
-                const int i = (int)L[k];
+                i = (int)L[k];
                 uint64_t x[W], z[W];
                 tile_key<W, T, I>(t, i, x, z);
 #pragma unroll
@@ -457,26 +539,34 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                         gm[w] &= gm[w] - 1;
                     }
                 }
+                bool more = false;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
                     t.g[(size_t)w * t.cap + i] = gm[w];
+                    more |= gm[w] != 0ull;
                     qx[w] = x[w] ^ tab.rx[gg][w];
                     qz[w] = z[w] ^ tab.rz[gg][w];
                 }
-                t.gi[i] = (uint8_t)gg;
                 j = tile_lookup_at<W, T, I>(t, qx, qz, &hslot);
-                // i R P = i^{1+e} (R xor P): sign of P's sin-branch into its partner
-                const int e = product_phase<W>(tab.rx[gg], tab.rz[gg], x, z);
-                const int phi = ((1 + e) & 3) == 0 ? 1 : -1;
+                // i R P = phi Q: sign of P's sin-branch into its partner Q
+                const int phi = branch_negative<W, T>(tab, gg, x, z) ? -1 : 1;
                 const T cs = tab.cs[gg], sn = tab.sn[gg];
-                const T c = t.c[i];
-                const T c2 = (j >= 0) ? t.c[j] : T(0);
-                if (j >= 0 && c2 != T(0)) {
+                const T c = ccur[i];
+                T c2 = T(0);
+                if (j >= 0) {
+                    // the partner's value before this gate: it is live and in
+                    // this round's list (stamp r, or r + 1 once its own thread
+                    // has written), or dead
+                    const uint8_t sj = t.sr[j];
+                    if (sj == stamp || sj == (uint8_t)r) c2 = ccur[j];
+                }
+                T ci;
+                if (c2 != T(0)) {
                     // both members of the pair rotate; the partner's contribution
                     // into P carries the opposite sign (i R Q = -phi P)
-                    t.cn[i] = Coef<T>::rot(cs, c, sn, c2, -phi);
+                    ci = Coef<T>::rot(cs, c, sn, c2, -phi);
                 } else {
-                    t.cn[i] = Coef<T>::mul(cs, c);
+                    ci = Coef<T>::mul(cs, c);
                     v = Coef<T>::mul(sn, c);
                     if (phi < 0) v = -v;
                     if (!Coef<T>::small(v, eps) && (p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max)) {
@@ -484,6 +574,13 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                         else create = true;
                     }
                 }
+                if (Coef<T>::small(ci, eps)) {
+                    ci = T(0);
+                    upd += gg + 1;
+                }
+                cnxt[i] = ci;
+                t.sr[i] = stamp;
+                keep = ci != T(0) && more;
             }
             // entry indices for new strings: one atomic per warp
             const unsigned cm = __ballot_sync(FULL, create);
@@ -512,7 +609,8 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
             if (born) {
                 // a new string, or one truncated earlier revived: it joins the
                 // orbit with the gates the orbit has left
-                t.c[idx] = v;
+                cnxt[idx] = v;
+                t.sr[idx] = stamp;
                 bool more = false;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -526,31 +624,11 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                 join = more;
                 upd -= gg + 1;
             }
-            act_append<W, T, I>(t, nxt, join, idx);
+            act_append<W, T, I>(t, nxt, (r + 1) % 3, keep, i);
+            act_append<W, T, I>(t, nxt, (r + 1) % 3, join, idx);
         }
         __syncthreads();
         if (*t.flag) return false;
-        for (int k0 = 0; k0 < na; k0 += nt) {
-            const int k = k0 + tid;
-            bool keep = false;
-            int i = 0;
-            if (k < na) {
-                i = (int)L[k];
-                T v = t.cn[i];
-                if (Coef<T>::small(v, eps)) {
-                    v = T(0);
-                    upd += (int)t.gi[i] + 1;
-                }
-                t.c[i] = v;
-                if (v != T(0)) {
-#pragma unroll
-                    for (int w = 0; w < W; ++w) keep |= t.g[(size_t)w * t.cap + i] != 0ull;
-                }
-            }
-            act_append<W, T, I>(t, nxt, keep, i);
-        }
-        if (tid == 0) t.nact[cur] = 0;
-        __syncthreads();
     }
     phase_mark(2);
 
@@ -562,7 +640,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
         const int nf = *t.n;
         int cnt = 0;
         for (int i = tid; i < nf; i += nt)
-            if (t.c[i] != T(0)) ++cnt;
+            if (tile_coef(t, i) != T(0)) ++cnt;
         upd += (long long)cnt * d.n_gates;
         int off = cnt ? atomicAdd(t.live, cnt) : 0;
         __syncthreads();
@@ -573,7 +651,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
         __syncthreads();
         unsigned long long pos = s_base + off;
         for (int i = tid; i < nf; i += nt) {
-            T c = t.c[i];
+            const T c = tile_coef(t, i);
             if (c == T(0)) continue;
             if (pos < p.dcap) {
 #pragma unroll
@@ -592,7 +670,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
         const int nf = *t.n;
         int cnt = 0;
         for (int i = tid; i < nf; i += nt) {
-            T c = t.c[i];
+            const T c = tile_coef(t, i);
             if (c == T(0)) continue;
             ++cnt;
             uint64_t x[W], z[W];
@@ -641,10 +719,10 @@ __device__ __forceinline__ Tile<W, T, I> carve_tile(unsigned char* mem, int cap,
     t.z = reinterpret_cast<uint64_t*>(q); q += sizeof(uint64_t) * W * cap;
     t.g = reinterpret_cast<uint64_t*>(q); q += sizeof(uint64_t) * W * cap;
     t.c = reinterpret_cast<T*>(q); q += sizeof(T) * cap;
-    t.cn = reinterpret_cast<T*>(q); q += sizeof(T) * cap;
+    t.c1 = reinterpret_cast<T*>(q); q += sizeof(T) * cap;
     t.hash = reinterpret_cast<I*>(q); q += sizeof(I) * t.hcap;
     t.act = reinterpret_cast<I*>(q); q += sizeof(I) * 2 * cap;
-    t.gi = reinterpret_cast<uint8_t*>(q); q += cap;
+    t.sr = reinterpret_cast<uint8_t*>(q); q += cap;
     t.n = ctl + 0;
     t.flag = ctl + 1;
     t.live = ctl + 2;
@@ -654,6 +732,11 @@ __device__ __forceinline__ Tile<W, T, I> carve_tile(unsigned char* mem, int cap,
 
 template <int W, typename T>
 __device__ __forceinline__ void load_gate_table(GateTab<W, T>& tab, const SubLayerDesc& d) {
+    if (threadIdx.x == 0) {
+        tab.cls = d.cls;
+        tab.shift = d.shift;
+        tab.psign = d.psign;
+    }
     for (int g = threadIdx.x; g < d.n_gates && g < 64 * W; g += blockDim.x) {
         int slot = d.cls == CLS_GENERIC ? g : d.slot_of[g];
         uint64_t rx[W], rz[W];
@@ -665,6 +748,7 @@ __device__ __forceinline__ void load_gate_table(GateTab<W, T>& tab, const SubLay
         }
         tab.cs[g] = T(d.cs[slot]);
         tab.sn[g] = T(d.sn[slot]);
+        tab.slot[g] = (uint8_t)slot;
     }
 }
 
@@ -672,7 +756,7 @@ __device__ __forceinline__ void load_gate_table(GateTab<W, T>& tab, const SubLay
 // buckets, or the list a smaller tier passed on); a bucket that does not fit is
 // passed to the next tier.
 template <int W, typename T, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_process(const StepParams p0, const StepParams* ps, int cap) {
+__global__ void __launch_bounds__(NT, NT <= 64 ? 4 : 1) k_process(const StepParams p0, const StepParams* ps, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int ctl[8];
     __shared__ uint32_t s_b;
@@ -682,7 +766,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_process(const StepParams p0, 
     if (!load_params(p, p0, ps)) return;
     Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem, cap, ctl);
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
-    if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
+    if (threadIdx.x == (NT > 32 ? 32 : 0) && p.next) make_act(*p.next, s_adn);
     load_gate_table<W, T>(tab, *p.desc);
     const uint32_t n_items = work_items(p);
     for (;;) {

@@ -144,20 +144,6 @@ __device__ __forceinline__ OrbTile<W, T> carve_orb(unsigned char* mem, OrbCaps k
 
 // ----------------------------------------------------------------------------- async copies
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ void cp_async_coef(float* smem, const float* gmem) { cp_async4(smem, gmem); }
-__device__ __forceinline__ void cp_async_coef(double* smem, const double* gmem) { cp_async8(smem, gmem); }
-
 // Starts copying bucket b's n_in strings (its region, then its grouped
 // overflow strings) into the tile's staging arrays; n_in <= O.  The warp
 // waits for them with cp_async_wait_all.
@@ -197,12 +183,6 @@ __device__ __forceinline__ uint32_t orb_hash(const uint64_t* x, const uint64_t* 
     }
     h *= 0xD6E8FEB86659FD93ULL;
     return (uint32_t)(h >> 32);
-}
-
-// Letter code (x + 2z) of qubit q of a string.
-template <int W>
-__device__ __forceinline__ int letter_at(const uint64_t* x, const uint64_t* z, int q) {
-    return (int)((x[q >> 6] >> (q & 63)) & 1ull) | ((int)((z[q >> 6] >> (q & 63)) & 1ull) << 1);
 }
 
 // x, z ^= the generators of the gates at the slots set in C.

@@ -60,11 +60,12 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
     long long upd = 0;   // this lane's share of the bucket's work count
     __syncwarp();
 
-    // ---- load: the bucket's region, then its overflow strings
+    // ---- load: the bucket's region, then its overflow strings, copied into
+    // the tile asynchronously (every lane's copies in flight at once), then
+    // entered into the hash table
     const size_t base = (size_t)b * p.sC;
     const size_t obase = ((uint64_t)n_in > p.sC) ? (size_t)p.soff[b] : 0;
     for (int i = lane; i < n_in; i += 32) {
-        uint64_t x[W], z[W];
         const bool reg = (uint64_t)i < p.sC;
         const size_t src = reg ? base + i : obase + (i - p.sC);
         const uint64_t* ax = reg ? p.sx : p.spx;
@@ -72,13 +73,18 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         const size_t acap = reg ? p.scap : p.spcap;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            x[w] = ax[(size_t)w * acap + src];
-            z[w] = az[(size_t)w * acap + src];
-            t.x[(size_t)w * t.cap + i] = x[w];
-            t.z[(size_t)w * t.cap + i] = z[w];
+            cp_async8(&t.x[(size_t)w * t.cap + i], &ax[(size_t)w * acap + src]);
+            cp_async8(&t.z[(size_t)w * t.cap + i], &az[(size_t)w * acap + src]);
         }
-        t.c[i] = load_coef<T>(reg ? p.sc : p.spc, src);
-        if (d.first) __threadfence_block();
+        cp_async_coef(&t.c[i], static_cast<const T*>(reg ? p.sc : p.spc) + src);
+        t.sr[i] = 0;
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+    for (int i = lane; i < n_in; i += 32) {
+        uint64_t x[W], z[W];
+        tile_key<W, T, int16_t>(t, i, x, z);
         tile_insert<W, T, int16_t>(t, i, x, z, d.first != 0);
     }
     __syncwarp();
@@ -108,8 +114,9 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 alive = true;
                 uint64_t A[W], Mx[W], Mz[W];
                 activity<W>(ad, x, z, A, Mx, Mz);
-                if (ad.cls == CLS_GENERIC) {
-                    gm[0] = A[0];
+                if (ad.ident) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) gm[w] = A[w];
                 } else {
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
@@ -137,18 +144,31 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
     if (*(volatile int*)t.flag) return false;
     phase_mark(1);
 
-    // ---- gate rounds (see process_bucket): lookup and rotation in one pass,
-    // then the commit; new-entry indices and list slots come from warp votes
+    // ---- gate rounds (see process_bucket): one pass per round.  Round r reads
+    // coefficients from buffer r & 1 and writes them to the other buffer, so a
+    // string and its partner both read the pair's values from before the gate;
+    // truncation, the work count and the next round's list are settled in the
+    // same pass.  New-entry indices and list slots come from warp votes.
     int n = n_in;
+    const bool tr = p.phase != nullptr;
+    unsigned st_rounds = 0, st_chunks = 0, st_listed = 0, st_pairs = 0, st_new = 0, st_rev = 0;
     for (int r = 0; r <= 64 * W && na > 0; ++r) {
+        if (tr) {
+            ++st_rounds;
+            st_chunks += (na + 31) >> 5;
+            st_listed += na;
+        }
         const int16_t* L = t.act + (size_t)(r & 1) * t.cap;
         int16_t* Ln = t.act + (size_t)((r & 1) ^ 1) * t.cap;
+        const T* ccur = t.cbuf(r & 1);
+        T* cnxt = t.cbuf((r & 1) ^ 1);
+        const uint8_t stamp = (uint8_t)(r + 1);
         int nn = 0;
         bool over = false;
         for (int k0 = 0; k0 < na; k0 += 32) {
             const int k = k0 + lane;
-            bool create = false, revive = false;
-            int i = 0, j = -1, gg = 0;
+            bool create = false, revive = false, keep = false;
+            int i = 0, j = -1;
             uint32_t hslot = 0;
             T v = T(0);
             uint64_t qx[W], qz[W], gm[W];
@@ -156,7 +176,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 i = (int)L[k];
                 uint64_t x[W], z[W];
                 tile_key<W, T, int16_t>(t, i, x, z);
-                gg = -1;
+                int gg = -1;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
                     gm[w] = t.g[(size_t)w * t.cap + i];
@@ -165,32 +185,53 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                         gm[w] &= gm[w] - 1;
                     }
                 }
+                bool more = false;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
                     t.g[(size_t)w * t.cap + i] = gm[w];
+                    more |= gm[w] != 0ull;
                     qx[w] = x[w] ^ tab.rx[gg][w];
                     qz[w] = z[w] ^ tab.rz[gg][w];
                 }
-                t.gi[i] = (uint8_t)gg;
                 j = tile_lookup_at<W, T, int16_t>(t, qx, qz, &hslot);
-                // i R P = i^{1+e} (R xor P): sign of P's sin-branch into its partner
-                const int e = product_phase<W>(tab.rx[gg], tab.rz[gg], x, z);
-                const int phi = ((1 + e) & 3) == 0 ? 1 : -1;
+                // i R P = phi Q: sign of P's sin-branch into its partner Q
+                const int phi = branch_negative<W, T>(tab, gg, x, z) ? -1 : 1;
                 const T cs = tab.cs[gg], sn = tab.sn[gg];
-                const T c = t.c[i];
-                const T c2 = (j >= 0) ? t.c[j] : T(0);
-                if (j >= 0 && c2 != T(0)) {
+                const T c = ccur[i];
+                T c2 = T(0);
+                if (j >= 0) {
+                    // the partner's value before this gate: it is live and in
+                    // this round's list (stamp r, or r + 1 once its own lane has
+                    // written), or dead
+                    const uint8_t sj = t.sr[j];
+                    if (sj == stamp || sj == (uint8_t)r) c2 = ccur[j];
+                }
+                T ci;
+                if (c2 != T(0)) {
                     // both members of the pair rotate; the partner's contribution
                     // into P carries the opposite sign (i R Q = -phi P)
-                    t.cn[i] = Coef<T>::rot(cs, c, sn, c2, -phi);
+                    ci = Coef<T>::rot(cs, c, sn, c2, -phi);
                 } else {
-                    t.cn[i] = Coef<T>::mul(cs, c);
+                    ci = Coef<T>::mul(cs, c);
                     v = Coef<T>::mul(sn, c);
                     if (phi < 0) v = -v;
                     if (!Coef<T>::small(v, eps) && (p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max)) {
                         if (j >= 0) revive = true;
                         else create = true;
                     }
+                }
+                if (Coef<T>::small(ci, eps)) {
+                    ci = T(0);
+                    upd += gg + 1;
+                }
+                cnxt[i] = ci;
+                t.sr[i] = stamp;
+                keep = ci != T(0) && more;
+                if (create || revive) upd -= gg + 1;
+                if (tr) {
+                    st_pairs += c2 != T(0);
+                    st_new += create;
+                    st_rev += revive;
                 }
             }
             const unsigned cm = __ballot_sync(FULL, create);
@@ -203,19 +244,19 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 }
             }
             n += __popc(cm);
-            if (create) {
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    t.x[(size_t)w * t.cap + idx] = qx[w];
-                    t.z[(size_t)w * t.cap + idx] = qz[w];
-                }
-            }
             bool join = false;
-            if (create || revive) upd -= gg + 1;
             if (create || revive) {
                 // a new string, or one truncated earlier revived: it joins the
                 // orbit with the gates the orbit has left
-                t.c[idx] = v;
+                if (create) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        t.x[(size_t)w * t.cap + idx] = qx[w];
+                        t.z[(size_t)w * t.cap + idx] = qz[w];
+                    }
+                }
+                cnxt[idx] = v;
+                t.sr[idx] = stamp;
                 bool more = false;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -228,7 +269,10 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 }
                 join = more;
             }
+            const unsigned km = __ballot_sync(FULL, keep);
             const unsigned jm = __ballot_sync(FULL, join);
+            if (keep) Ln[nn + __popc(km & lt)] = (int16_t)i;
+            nn += __popc(km);
             if (join) Ln[nn + __popc(jm & lt)] = (int16_t)idx;
             nn += __popc(jm);
         }
@@ -238,39 +282,34 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
             if (lane == 0) *t.flag = any_over ? (int)FAIL_POOL : (int)FAIL_HASH;
             return false;
         }
-        __syncwarp();
-        for (int k0 = 0; k0 < na; k0 += 32) {
-            const int k = k0 + lane;
-            bool keep = false;
-            int i = 0;
-            if (k < na) {
-                i = (int)L[k];
-                T v = t.cn[i];
-                if (Coef<T>::small(v, eps)) {
-                    v = T(0);
-                    upd += (int)t.gi[i] + 1;
-                }
-                t.c[i] = v;
-                if (v != T(0)) {
-#pragma unroll
-                    for (int w = 0; w < W; ++w) keep |= t.g[(size_t)w * t.cap + i] != 0ull;
-                }
-            }
-            const unsigned km = __ballot_sync(FULL, keep);
-            if (keep) Ln[nn + __popc(km & lt)] = (int16_t)i;
-            nn += __popc(km);
-        }
-        __syncwarp();
         na = nn;
     }
 
     phase_mark(2);
+    if (p.phase) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            st_pairs += __shfl_xor_sync(FULL, st_pairs, o);
+            st_new += __shfl_xor_sync(FULL, st_new, o);
+            st_rev += __shfl_xor_sync(FULL, st_rev, o);
+        }
+        if (lane == 0) {
+            unsigned long long* q = p.phase + (CTR_STAT - CTR_PHASE);
+            atomicAdd(q + 0, 1ull);
+            atomicAdd(q + 1, (unsigned long long)st_rounds);
+            atomicAdd(q + 2, (unsigned long long)st_chunks);
+            atomicAdd(q + 3, (unsigned long long)st_listed);
+            atomicAdd(q + 4, (unsigned long long)st_pairs);
+            atomicAdd(q + 5, (unsigned long long)st_new);
+            atomicAdd(q + 6, (unsigned long long)st_rev);
+        }
+    }
 
     // ---- output
     unsigned long long emitted = 0;
     if (d.final_) {
         int cnt = 0;
-        for (int i = lane; i < n; i += 32) cnt += t.c[i] != T(0);
+        for (int i = lane; i < n; i += 32) cnt += tile_coef(t, i) != T(0);
         upd += (long long)cnt * d.n_gates;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
@@ -279,7 +318,8 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         pos = __shfl_sync(FULL, pos, 0);
         for (int i0 = 0; i0 < n; i0 += 32) {
             const int i = i0 + lane;
-            const bool lv = i < n && t.c[i] != T(0);
+            const T ci = i < n ? tile_coef(t, i) : T(0);
+            const bool lv = ci != T(0);
             const unsigned lm = __ballot_sync(FULL, lv);
             if (lv) {
                 const unsigned long long q = pos + __popc(lm & lt);
@@ -289,7 +329,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                         p.dx[(size_t)w * p.dcap + q] = t.x[(size_t)w * t.cap + i];
                         p.dz[(size_t)w * p.dcap + q] = t.z[(size_t)w * t.cap + i];
                     }
-                    static_cast<T*>(p.dc)[q] = t.c[i];
+                    static_cast<T*>(p.dc)[q] = ci;
                 } else {
                     atomicAdd(&p.counters[CTR_ERR_REGION], 1ull);
                 }
@@ -301,7 +341,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         const uint32_t bmask = p.dB - 1;
         int cnt = 0;
         for (int i = lane; i < n; i += 32) {
-            T c = t.c[i];
+            const T c = tile_coef(t, i);
             if (c == T(0)) continue;
             ++cnt;
             uint64_t x[W], z[W];
