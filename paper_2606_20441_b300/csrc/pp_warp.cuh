@@ -338,16 +338,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         }
         emitted = (unsigned long long)cnt;
     } else {
-        const uint32_t bmask = p.dB - 1;
-        int cnt = 0;
-        for (int i = lane; i < n; i += 32) {
-            const T c = tile_coef(t, i);
-            if (c == T(0)) continue;
-            ++cnt;
-            uint64_t x[W], z[W];
-            tile_key<W, T, int16_t>(t, i, x, z);
-            emit<W, T>(p, bucket_of<W>(adn, x, z, bmask), x, z, c);
-        }
+        int cnt = emit_tile<1, W, T, int16_t>(t, adn, p, lane, 32, n);
         upd += (long long)cnt * d.n_gates;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
