@@ -193,7 +193,11 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                     qx[w] = x[w] ^ tab.rx[gg][w];
                     qz[w] = z[w] ^ tab.rz[gg][w];
                 }
-                j = tile_lookup_at<W, T, int16_t>(t, qx, qz, &hslot);
+                // a partner over the weight cap is never in the tile (every
+                // string that enters it is within the cap, or is killed in the
+                // prologue before any gate), and is never created
+                const bool reach = p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max;
+                if (reach) j = tile_lookup_at<W, T, int16_t>(t, qx, qz, &hslot);
                 // i R P = phi Q: sign of P's sin-branch into its partner Q
                 const int phi = branch_negative<W, T>(tab, gg, x, z) ? -1 : 1;
                 const T cs = tab.cs[gg], sn = tab.sn[gg];
@@ -215,7 +219,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                     ci = Coef<T>::mul(cs, c);
                     v = Coef<T>::mul(sn, c);
                     if (phi < 0) v = -v;
-                    if (!Coef<T>::small(v, eps) && (p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max)) {
+                    if (reach && !Coef<T>::small(v, eps)) {
                         if (j >= 0) revive = true;
                         else create = true;
                     }
