@@ -333,9 +333,9 @@ def ours_arm(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     updates, launches = 0.0, 0
-    tier_ms = [0.0] * 4
-    tier_strings = [0.0] * 4
-    tier_launches = [0] * 4
+    tier_ms = [0.0] * pp.N_TIERS
+    tier_strings = [0.0] * pp.N_TIERS
+    tier_launches = [0] * pp.N_TIERS
     expect = None
     for _ in range(args.steps):
         h.run_instance(inst)
@@ -343,7 +343,7 @@ def ours_arm(args, rank, world, local_rank):
         s = h.pp_get_stats()
         updates += s.updates
         launches += s.kernel_launches
-        for t in range(4):
+        for t in range(pp.N_TIERS):
             tier_ms[t] += s.tier_ms[t]
             tier_strings[t] += s.tier_strings[t]
             tier_launches[t] += s.tier_launches[t]

@@ -210,12 +210,13 @@ typedef struct {
     int kernel_launches;     /* kernels this library launched in the last propagation  */
     int fallback_buckets;    /* buckets processed by the global-memory path            */
     double seconds;          /* wall time of the last pp_propagate (host clock)        */
-    /* per processing tier (0..2: shared-memory tiles of growing size, 3: global-memory
-       tile): launches, summed device time from CUDA events on the handle's stream, and
-       strings read + written by completed buckets */
-    int tier_launches[4];
-    double tier_ms[4];
-    double tier_strings[4];
+    /* per processing tier (0, 1: one warp per bucket, tiles of 248 and 512 strings;
+       2, 3: one CTA per bucket, tiles of 1024 and 4096 strings; 4: global-memory tile):
+       launches, summed device time from CUDA events on the handle's stream, and strings
+       read + written by completed buckets */
+    int tier_launches[5];
+    double tier_ms[5];
+    double tier_strings[5];
     double bytes_per_string;  /* bytes of one stored string (x, z words and coefficient) */
     int orbit_launches;       /* tier-0 launches that used the orbit tiles (the rest of
                                  tier 0 used the sparse warp tiles)                      */
@@ -242,10 +243,10 @@ const char* pp_last_error(const pp_handle* h);
  *                    sub-layer's observed growth, times this factor, fill one
  *                    warp tile; in [1, 16]; 0 = library default (2.4).  Larger
  *                    values mean more, emptier buckets.
- *   first_tier       0..3: buckets start at this processing tier (0: orbit or
- *                    sparse warp tiles, 1 and 2: CTA tiles in shared memory, 3:
- *                    the global-memory tile); tiers below it pass every bucket
- *                    on.  0 (default) is the fastest; the others exist so that
+ *   first_tier       0..4: buckets start at this processing tier (0: orbit or
+ *                    sparse warp tiles, 1: larger warp tiles, 2 and 3: CTA
+ *                    tiles in shared memory, 4: the global-memory tile); tiers
+ *                    below it pass every bucket on.  0 (default) is the fastest; the others exist so that
  *                    tests can run every tier on small inputs.
  *   orbit_tiles      1: class sub-layers are planned as single runs of gates
  *                    with disjoint supports and tier 0 processes them with the

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <string>
 #include <memory>
 #include <tuple>
 #include <thread>
@@ -43,11 +44,13 @@ struct TierCfg {
 #ifndef PP_TIER1_THREADS
 #define PP_TIER1_THREADS 64
 #endif
+constexpr int WARP_TILE_WARPS2 = 2;   // warps per CTA of the second warp tier
 #ifndef PP_TIER2_THREADS
 #define PP_TIER2_THREADS 256
 #endif
 constexpr TierCfg kTiers[N_TIERS] = {
-    {32 * WARP_TILE_WARPS, 248, 248},   // one warp per bucket
+    {32 * WARP_TILE_WARPS, 248, 248},   // one warp per bucket, 4 warps per CTA
+    {32 * WARP_TILE_WARPS2, 512, 384},  // one warp per bucket, larger tiles, 2 warps per CTA
     {PP_TIER1_THREADS, 1024, 1024},     // CTA tiles: few warps, so that a round's
     {PP_TIER2_THREADS, 4096, 2048},     // barriers wait on few warps
     {512, 1 << 20, 1 << 20}};           // global-memory tile
@@ -117,7 +120,7 @@ struct pp_handle {
     uint32_t* fill[2] = {nullptr, nullptr};
     uint32_t fill_cap = 0;
     unsigned long long* counters = nullptr;
-    uint32_t* pass_list[N_TIERS - 1] = {nullptr, nullptr, nullptr};   // buckets passed tier t -> t+1
+    uint32_t* pass_list[N_TIERS - 1] = {};   // buckets passed tier t -> t+1
     size_t spill_cap = 0;          // overflow strings per layout
     Arena spill_raw, spill_grp;
     uint32_t* spill_b = nullptr;
@@ -544,7 +547,7 @@ struct CapMem {
     uint32_t* spill_s = nullptr;
     uint32_t* fill[2] = {nullptr, nullptr};
     uint64_t* soff[2] = {nullptr, nullptr};
-    uint32_t* pass_list[N_TIERS - 1] = {nullptr, nullptr, nullptr};
+    uint32_t* pass_list[N_TIERS - 1] = {};
     unsigned char* fb_scratch = nullptr;
     size_t fb_slice = 0;
     int fb_cap = 0;
@@ -596,9 +599,9 @@ void free_cap_memory(pp_handle* h, CapMem& m) {
     for (Arena* a : {&m.arena[0], &m.arena[1], &m.spill_raw, &m.spill_grp})
         for (void* q : {(void*)a->x, (void*)a->z, a->c}) dev_free(h, q);
     for (void* q : {(void*)m.spill_b, (void*)m.spill_s, (void*)m.fill[0], (void*)m.fill[1], (void*)m.soff[0],
-                    (void*)m.soff[1], (void*)m.pass_list[0], (void*)m.pass_list[1], (void*)m.pass_list[2],
-                    (void*)m.fb_scratch})
+                    (void*)m.soff[1], (void*)m.fb_scratch})
         dev_free(h, q);
+    for (uint32_t* q : m.pass_list) dev_free(h, q);
     m = CapMem();
 }
 
@@ -756,7 +759,7 @@ uint32_t pow2_at_least(double v, uint32_t cap) {
 struct KernelFacts {
     static constexpr int kDevices = 64;
     std::atomic<size_t> attr[kDevices];
-    std::atomic<int> occ[kDevices];
+    std::atomic<unsigned long long> occ[kDevices];   // resident CTAs << 32 | dynamic smem they were counted for
     KernelFacts() {
         for (int i = 0; i < kDevices; ++i) {
             attr[i].store(0);
@@ -774,12 +777,13 @@ cudaError_t prepare_kernel(const pp_handle* h, KernelFacts& f, K kernel, int thr
         if (e != cudaSuccess) return e;
         f.attr[dev].store(smem);
     }
-    int n = f.occ[dev].load();
-    if (n == 0) {
+    const unsigned long long o = f.occ[dev].load();
+    int n = (int)(o >> 32);
+    if (n == 0 || (o & 0xffffffffull) != (unsigned long long)smem) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
         if (e != cudaSuccess) return e;
         n = std::max(n, 1);
-        f.occ[dev].store(n);
+        f.occ[dev].store(((unsigned long long)n << 32) | (unsigned long long)(uint32_t)smem);
     }
     *per_sm = n;
     return cudaSuccess;
@@ -803,6 +807,21 @@ cudaError_t launch_smem_tier(pp_handle* h, const StepParams& p, int cap, uint32_
     if (e != cudaSuccess) return e;
     uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(per_sm * h->sm_count));
     k_process<W, T, NT><<<dim3(grid, rows.n), NT, smem, h->st>>>(p, rows.ps, cap);
+    return cudaGetLastError();
+}
+
+// A tier whose tiles are processed one warp per bucket (pp_warp.cuh), NW
+// warps per CTA.
+template <int W, typename T, int NW>
+cudaError_t launch_warp_tier(pp_handle* h, const StepParams& p, int cap, uint32_t n_items, const LaunchRows& rows) {
+    const size_t smem = warp_tile_bytes<W, T>((size_t)cap) * NW;
+    static KernelFacts facts;
+    int per_sm = 1;
+    cudaError_t e = prepare_kernel(h, facts, k_process_warp<W, T, NW>, 32 * NW, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    const uint32_t want = n_items == UINT32_MAX ? UINT32_MAX : (n_items + NW - 1) / NW;
+    uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(want, 1), (uint32_t)(per_sm * h->sm_count));
+    k_process_warp<W, T, NW><<<dim3(grid, rows.n), 32 * NW, smem, h->st>>>(p, rows.ps, cap);
     return cudaGetLastError();
 }
 
@@ -842,18 +861,11 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orb
                 k_process_orbit<W, T><<<dim3(grid, rows.n), 32 * ORB_WARPS, smem, h->st>>>(p, rows.ps, K);
                 return cudaGetLastError();
             }
-            const size_t smem = warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS;
-            static KernelFacts facts;
-            int per_sm = 1;
-            cudaError_t e = prepare_kernel(h, facts, k_process_warp<W, T>, kTiers[0].threads, smem, &per_sm);
-            if (e != cudaSuccess) return e;
-            uint32_t grid = std::min<uint32_t>(std::max<uint32_t>((n_items + WARP_TILE_WARPS - 1) / WARP_TILE_WARPS, 1),
-                                               (uint32_t)(per_sm * h->sm_count));
-            k_process_warp<W, T><<<dim3(grid, rows.n), kTiers[0].threads, smem, h->st>>>(p, rows.ps, cap);
-            return cudaGetLastError();
+            return launch_warp_tier<W, T, WARP_TILE_WARPS>(h, p, cap, n_items, rows);
         }
-        case 1: return launch_smem_tier<W, T, kTiers[1].threads>(h, p, cap, n_items, rows);
+        case 1: return launch_warp_tier<W, T, WARP_TILE_WARPS2>(h, p, cap, n_items, rows);
         case 2: return launch_smem_tier<W, T, kTiers[2].threads>(h, p, cap, n_items, rows);
+        case 3: return launch_smem_tier<W, T, kTiers[3].threads>(h, p, cap, n_items, rows);
         default: {
             uint32_t grid = std::min<uint32_t>(n_items, (uint32_t)kFallbackCTAs);
             k_process_global<W, T><<<dim3(grid, rows.n), kTiers[kGlobalTier].threads, 0, h->st>>>(
@@ -864,14 +876,15 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orb
     }
 }
 
-// Tile entries of a shared-memory tier; PP_TILE_CAPS="c0,c1,c2" overrides the
-// table for measurements.
+// Tile entries of a shared-memory tier; PP_TILE_CAPS="c0,c1,c2,c3" overrides
+// the table for measurements.
 int tier_cap(const pp_handle* h, int tier) {
     int c = h->W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2;
     if (tier < kGlobalTier) {
         if (const char* e = getenv("PP_TILE_CAPS")) {
-            int v[3] = {0, 0, 0};
-            if (sscanf(e, "%d,%d,%d", &v[0], &v[1], &v[2]) == 3 && v[tier] >= 64 && v[tier] <= 8192) c = v[tier];
+            int v[4] = {0, 0, 0, 0};
+            if (sscanf(e, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4 && v[tier] >= 64 && v[tier] <= 8192)
+                c = v[tier];
         }
     }
     return c;
@@ -1128,7 +1141,7 @@ struct Prop {
     FILE* trace = nullptr;
     unsigned long long* ctr_dev = nullptr;   // the counters this propagation uses
     unsigned long long ctr[CTR_COUNT];
-    float ms[N_TIERS] = {0.f, 0.f, 0.f, 0.f};
+    float ms[N_TIERS] = {};
     bool finished = false;
     Prop() { std::memset(&p, 0, sizeof(p)); }
     ~Prop() {
@@ -1358,7 +1371,8 @@ pp_status prop_finish(Prop& P) {
         P.stats.tier_ms[tier] += P.ms[tier];
         P.stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];
     }
-    unsigned long long passed[N_TIERS] = {ctr[CTR_DEFER], ctr[CTR_DEFER + 1], ctr[CTR_DEFER + 2], 0};
+    unsigned long long passed[N_TIERS] = {};
+    for (int tier = 0; tier + 1 < N_TIERS; ++tier) passed[tier] = ctr[CTR_DEFER + tier];
     P.stats.fallback_buckets += (int)passed[kGlobalTier - 1];
     if (ctr[CTR_ERR_FALLBACK])
         return fail(h, PP_ERR_CAPACITY, "sub-layer %d: a bucket exceeds the global tile (%d strings)", s, h->fb_cap);
@@ -1404,23 +1418,31 @@ pp_status prop_finish(Prop& P) {
         }
         Nout = h->top_k;
     }
-    if (P.trace)
+    if (P.trace) {
+        // one JSON line per sub-layer (PP_TRACE): sizes, per-tier figures, failures
+        auto list = [](const unsigned long long* v, int n, int stride = 1) {
+            std::string t = "[";
+            for (int k = 0; k < n; ++k) t += (k ? ", " : "") + std::to_string(v[k * stride]);
+            return t + "]";
+        };
+        std::string ms = "[", ts = "[";
+        for (int tier = 0; tier < N_TIERS; ++tier) {
+            char b[64];
+            snprintf(b, sizeof(b), "%s%.4f", tier ? ", " : "", P.ms[tier]);
+            ms += b;
+            ts += (tier ? ", " : "") + std::to_string(ctr[CTR_LOADED + tier] + ctr[CTR_EMITTED + tier]);
+        }
+        ms += "]";
+        ts += "]";
         fprintf(P.trace,
                 "{\"sub\": %d, \"cls\": %d, \"gates\": %d, \"orbit\": %d, \"n_in\": %zu, \"n_out\": %zu, "
-                "\"buckets_in\": %u, \"buckets_out\": %u, \"passed\": [%llu, %llu, %llu], "
-                "\"spill\": %llu, \"ms\": [%.4f, %.4f, %.4f, %.4f], "
-                "\"tier_strings\": [%llu, %llu, %llu, %llu], "
-                "\"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
-                "\"t0_cycles\": [%llu, %llu, %llu, %llu], \"cta_cycles\": [%llu, %llu, %llu, %llu], "
-                "\"t0_stat\": [%llu, %llu, %llu, %llu, %llu, %llu, %llu]}\n",
-                s, d.cls, d.n_gates, (int)P.use_orbit(s), P.N, Nout, P.B, P.nB, passed[0], passed[1], passed[2],
-                n_spill_out, P.ms[0], P.ms[1], P.ms[2], P.ms[3],
-                ctr[CTR_LOADED] + ctr[CTR_EMITTED], ctr[CTR_LOADED + 1] + ctr[CTR_EMITTED + 1],
-                ctr[CTR_LOADED + 2] + ctr[CTR_EMITTED + 2], ctr[CTR_LOADED + 3] + ctr[CTR_EMITTED + 3],
-                ctr[CTR_FAIL], ctr[CTR_FAIL + 1], ctr[CTR_FAIL + 2], ctr[CTR_PHASE], ctr[CTR_PHASE + 1],
-                ctr[CTR_PHASE + 2], ctr[CTR_PHASE + 3], ctr[CTR_PHASE_CTA], ctr[CTR_PHASE_CTA + 1],
-                ctr[CTR_PHASE_CTA + 2], ctr[CTR_PHASE_CTA + 3], ctr[CTR_STAT], ctr[CTR_STAT + 1],
-                ctr[CTR_STAT + 2], ctr[CTR_STAT + 3], ctr[CTR_STAT + 4], ctr[CTR_STAT + 5], ctr[CTR_STAT + 6]);
+                "\"buckets_in\": %u, \"buckets_out\": %u, \"passed\": %s, \"spill\": %llu, \"ms\": %s, "
+                "\"tier_strings\": %s, \"fail_load\": %llu, \"fail_pool\": %llu, \"fail_hash\": %llu, "
+                "\"t0_cycles\": %s, \"cta_cycles\": %s, \"t0_stat\": %s}\n",
+                s, d.cls, d.n_gates, (int)P.use_orbit(s), P.N, Nout, P.B, P.nB, list(passed, N_TIERS - 1).c_str(),
+                n_spill_out, ms.c_str(), ts.c_str(), ctr[CTR_FAIL], ctr[CTR_FAIL + 1], ctr[CTR_FAIL + 2],
+                list(ctr + CTR_PHASE, 4).c_str(), list(ctr + CTR_PHASE_CTA, 4).c_str(), list(ctr + CTR_STAT, 7).c_str());
+    }
     if (P.N > 0) P.growth[h->sub_kind[s]] = std::max(0.05, (double)Nout / (double)P.N);
     P.N = Nout;
     P.n_over_in = n_spill_out;
@@ -1697,7 +1719,7 @@ pp_status pp_set_tuning(pp_handle* h, const pp_tuning* t) {
         return fail(h, PP_ERR_ARG, "max_fused_gates must be 0 (default) or 1..64*W");
     if (t->bucket_headroom != 0.0 && !(t->bucket_headroom >= 1.0 && t->bucket_headroom <= 16.0))
         return fail(h, PP_ERR_ARG, "bucket_headroom must be 0 (default) or in [1, 16]");
-    if (t->first_tier < 0 || t->first_tier >= N_TIERS) return fail(h, PP_ERR_ARG, "first_tier must be in 0..3");
+    if (t->first_tier < 0 || t->first_tier >= N_TIERS) return fail(h, PP_ERR_ARG, "first_tier must be in 0..4");
     if (t->orbit_tiles != 0 && t->orbit_tiles != 1) return fail(h, PP_ERR_ARG, "orbit_tiles must be 0 or 1");
     if (t->max_fused_gates != h->tune.max_fused_gates || t->orbit_tiles != h->tune.orbit_tiles) h->subs_dirty = true;
     h->tune = *t;

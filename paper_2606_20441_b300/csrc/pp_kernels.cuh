@@ -65,24 +65,25 @@ struct StepParams {
                                   // accumulated when tracing; nullptr otherwise
 };
 
+constexpr int N_TIERS = 5;   // warp tiles (two sizes), CTA tiles (two sizes), global-memory tile
+
 enum {
-    CTR_WORK = 0,        // work queues, one per tier (0..3)
-    CTR_OUT = 4,         // terms written (next layout or final)
-    CTR_PROLOGUE = 5,    // (unused)
-    CTR_DEFER = 6,       // buckets passed from tier t to tier t+1 (6..8)
-    CTR_ERR_REGION = 9,  // strings dropped: overflow area or result full
-    CTR_ERR_FALLBACK = 10, // buckets too large even for the global tier
-    CTR_SPILL = 11,      // strings written to the destination overflow area
-    CTR_LOADED = 12,     // strings loaded by completed buckets, per tier (12..15)
-    CTR_EMITTED = 16,    // strings written by completed buckets, per tier (16..19)
-    CTR_FAIL = 20,       // buckets passed on, by reason (20..23): load, entry pool, hash, list
-    CTR_SPILL_TOTAL = 24,// scratch of the overflow grouping
-    CTR_PHASE = 28,      // tier-0 cycles per phase when tracing (28..31)
-    CTR_PHASE_CTA = 32,  // CTA-tier cycles per phase when tracing (32..35)
-    CTR_UPDATES = 36,    // canonical work count of the completed buckets (string lifetimes)
-    CTR_STAT = 37,       // tier-0 work statistics when tracing (37..44): buckets, rounds,
+    CTR_WORK = 0,        // work queues, one per tier (0..N_TIERS-1)
+    CTR_OUT = N_TIERS,   // terms written (next layout or final)
+    CTR_DEFER = CTR_OUT + 1,                // buckets passed from tier t to tier t+1 (N_TIERS - 1)
+    CTR_ERR_REGION = CTR_DEFER + N_TIERS - 1,  // strings dropped: overflow area or result full
+    CTR_ERR_FALLBACK,    // buckets too large even for the global tier
+    CTR_SPILL,           // strings written to the destination overflow area
+    CTR_LOADED,          // strings loaded by completed buckets, per tier (N_TIERS)
+    CTR_EMITTED = CTR_LOADED + N_TIERS,     // strings written by completed buckets, per tier
+    CTR_FAIL = CTR_EMITTED + N_TIERS,       // buckets passed on, by reason (4): load, entry pool, hash, list
+    CTR_SPILL_TOTAL = CTR_FAIL + 4,         // scratch of the overflow grouping
+    CTR_PHASE,           // warp-tier cycles per phase when tracing (4)
+    CTR_PHASE_CTA = CTR_PHASE + 4,          // CTA-tier cycles per phase when tracing (4)
+    CTR_UPDATES = CTR_PHASE_CTA + 4,        // canonical work count of the completed buckets (string lifetimes)
+    CTR_STAT,            // tier-0 work statistics when tracing (8): buckets, rounds,
                          // list chunks, listed strings, live pairs, created, revived, 0
-    CTR_COUNT = 45
+    CTR_COUNT = CTR_STAT + 8
 };
 
 // Number of work items (buckets) of a tier launch.
@@ -108,7 +109,6 @@ __device__ __forceinline__ bool load_params(StepParams& dst, const StepParams& p
     return s_left != 0;
 }
 
-constexpr int N_TIERS = 4;
 constexpr int NSPILL = 64;   // shards of the overflow area (one atomic counter each)
 
 enum { FAIL_LOAD = 1, FAIL_POOL = 2, FAIL_HASH = 3, FAIL_CHUNK = 4 };

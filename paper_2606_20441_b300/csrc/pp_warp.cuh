@@ -358,12 +358,11 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
     return true;
 }
 
-template <int W, typename T>
-__global__ void __launch_bounds__(32 * WARP_TILE_WARPS, 5) k_process_warp(const StepParams p0, const StepParams* ps,
-                                                                           int cap) {
+template <int W, typename T, int NW>
+__global__ void __launch_bounds__(32 * NW, 5) k_process_warp(const StepParams p0, const StepParams* ps, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ GateTab<W, T> tab;
-    __shared__ int s_ctl[WARP_TILE_WARPS][8];
+    __shared__ int s_ctl[NW][8];
     __shared__ unsigned long long s_acc[3];
     __shared__ ActDesc s_ad, s_adn;
     __shared__ StepParams p;
@@ -371,7 +370,7 @@ __global__ void __launch_bounds__(32 * WARP_TILE_WARPS, 5) k_process_warp(const 
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < 3) s_acc[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
-    if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
+    if (threadIdx.x == (NW > 1 ? 32 : 0) && p.next) make_act(*p.next, s_adn);
     load_gate_table<W, T>(tab, *p.desc);
     __syncthreads();
 

@@ -20,6 +20,7 @@ from . import inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpp.so")
+N_TIERS = 5   # processing tiers (pp_stats.tier_*)
 
 PP_OK, PP_ERR_ARG, PP_ERR_STATE, PP_ERR_NOMEM, PP_ERR_CAPACITY, PP_ERR_CUDA, PP_ERR_TIMEOUT = range(7)
 STATUS_NAMES = {0: "PP_OK", 1: "PP_ERR_ARG", 2: "PP_ERR_STATE", 3: "PP_ERR_NOMEM",
@@ -49,9 +50,9 @@ class pp_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int),
                 ("fallback_buckets", ctypes.c_int),
                 ("seconds", ctypes.c_double),
-                ("tier_launches", ctypes.c_int * 4),
-                ("tier_ms", ctypes.c_double * 4),
-                ("tier_strings", ctypes.c_double * 4),
+                ("tier_launches", ctypes.c_int * N_TIERS),
+                ("tier_ms", ctypes.c_double * N_TIERS),
+                ("tier_strings", ctypes.c_double * N_TIERS),
                 ("bytes_per_string", ctypes.c_double),
                 ("orbit_launches", ctypes.c_int),
                 ("retries", ctypes.c_int),
