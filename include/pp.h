@@ -241,7 +241,7 @@ const char* pp_last_error(const pp_handle* h);
  *                    per bucket.
  *   bucket_headroom  buckets are sized so that a bucket's strings times the
  *                    sub-layer's observed growth, times this factor, fill one
- *                    warp tile; in [1, 16]; 0 = library default (2.4).  Larger
+ *                    warp tile; in [1, 16]; 0 = library default (2.0).  Larger
  *                    values mean more, emptier buckets.
  *   first_tier       0..4: buckets start at this processing tier (0: orbit or
  *                    sparse warp tiles, 1: larger warp tiles, 2 and 3: CTA

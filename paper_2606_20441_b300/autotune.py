@@ -24,8 +24,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 Setting = Tuple[int, float]   # (max_fused_gates, bucket_headroom)
 
-# (0, 0.0) is the library default (whole layers, headroom 2.4)
-CANDIDATES: List[Setting] = [(0, 0.0), (32, 2.4), (16, 1.6), (64, 1.8), (32, 1.6), (64, 3.2)]
+# (0, 0.0) is the library default (whole layers, headroom 2.0)
+CANDIDATES: List[Setting] = [(0, 0.0), (32, 2.4), (16, 1.6), (64, 1.6), (32, 2.0), (64, 2.8)]
 
 
 def class_key(inst) -> str:

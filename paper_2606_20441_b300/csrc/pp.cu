@@ -266,7 +266,7 @@ int max_fused_gates(const pp_handle* h) {
 }
 
 double bucket_headroom(const pp_handle* h) {
-    return h->tune.bucket_headroom > 0.0 ? h->tune.bucket_headroom : 2.4;
+    return h->tune.bucket_headroom > 0.0 ? h->tune.bucket_headroom : 2.0;
 }
 
 // Marks class sub-layers as orbit sub-layers and fills their letter table:

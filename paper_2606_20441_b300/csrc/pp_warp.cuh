@@ -358,8 +358,12 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
     return true;
 }
 
+#ifndef PP_WARP_MIN_BLOCKS
+#define PP_WARP_MIN_BLOCKS 5   // resident CTAs per SM the register budget is sized for
+#endif
 template <int W, typename T, int NW>
-__global__ void __launch_bounds__(32 * NW, 5) k_process_warp(const StepParams p0, const StepParams* ps, int cap) {
+__global__ void __launch_bounds__(32 * NW, PP_WARP_MIN_BLOCKS) k_process_warp(const StepParams p0, const StepParams* ps,
+                                                                             int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ GateTab<W, T> tab;
     __shared__ int s_ctl[NW][8];

@@ -45,7 +45,7 @@ def test_every_setting_gives_identical_results(pp, precision):
 
 def test_tuning_arguments(pp):
     h = pp.Handle(40)
-    assert h.pp_get_tuning() == (64, 2.4)
+    assert h.pp_get_tuning() == (64, 2.0)
     h.pp_set_tuning(24, 2.5)
     assert h.pp_get_tuning() == (24, 2.5)
     for bad in [(65, 1.6), (-1, 1.6), (16, 0.5), (16, 17.0)]:
@@ -53,7 +53,7 @@ def test_tuning_arguments(pp):
             h.pp_set_tuning(*bad)
         assert h.pp_get_tuning() == (24, 2.5)
     h.pp_set_tuning(0, 0.0)
-    assert h.pp_get_tuning() == (64, 2.4)
+    assert h.pp_get_tuning() == (64, 2.0)
     h.close()
     h2 = pp.Handle(100)
     h2.pp_set_tuning(128, 1.6)
