@@ -115,7 +115,10 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
                         const uint64_t* ez, const double* lambda, int mode);
 
 /* Propagates O = sum_t oc[t] P(ox[t], oz[t]) backwards through every layer.
- *   ox, oz [n_terms][W], oc [n_terms]; duplicate strings are summed.
+ *   ox, oz [n_terms][W], oc [n_terms] (finite, |oc| < 2^32, else PP_ERR_ARG);
+ *          duplicate strings are summed on the device exactly, independently of
+ *          their order (128-bit fixed point, units of 2^-80, rounded once to the
+ *          nearest double; a duplicated string's terms below 2^-80 are lost).
  *   eps    coefficient threshold (>= 0; 0 keeps every nonzero term)
  *   w_max  Pauli-weight cap (< 0: none)
  * The host waits for the device once per fused sub-layer (to size the next

@@ -905,20 +905,31 @@ int orbit_load_cap(const pp_handle* h) {
     return h->opt.precision == PP_PRECISION_FP32 ? orbit_caps<2, float>().O : orbit_caps<2, double>().O;
 }
 
-cudaError_t dispatch_scatter(pp_handle* h, const uint64_t* ox, const uint64_t* oz, const double* oc,
-                             size_t n, const StepParams& p, int* launches) {
-    bool f32 = h->opt.precision == PP_PRECISION_FP32;
-    int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
-    grid = std::max(grid, 1);
-    if (h->W == 1) {
-        if (f32) k_scatter_input<1, float><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
-        else k_scatter_input<1, double><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
-    } else {
-        if (f32) k_scatter_input<2, float><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
-        else k_scatter_input<2, double><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, p);
-    }
-    ++*launches;
+// Slots of the input-merge hash table for n input strings (load factor <= 1/2).
+size_t input_merge_slots(size_t n) {
+    size_t H = 64;
+    while (H < 2 * n) H <<= 1;
+    return H;
+}
+
+// Merges duplicate input strings (k_input_claim, k_input_accumulate) and
+// scatters the merged observable into the first sub-layer's buckets.  `m`
+// points at zeroed counts and accumulators and owners set to -1.
+template <int W>
+cudaError_t launch_input(pp_handle* h, const uint64_t* ox, const uint64_t* oz, const double* oc, size_t n,
+                         const InputMerge& m, const StepParams& p) {
+    const int grid = (int)std::max<size_t>(std::min<size_t>((n + 255) / 256, 4096), 1);
+    k_input_claim<W><<<grid, 256, 0, h->st>>>(ox, oz, n, m);
+    k_input_accumulate<W><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, m);
+    if (h->opt.precision == PP_PRECISION_FP32) k_scatter_input<W, float><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, m, p);
+    else k_scatter_input<W, double><<<grid, 256, 0, h->st>>>(ox, oz, oc, n, m, p);
     return cudaGetLastError();
+}
+
+cudaError_t dispatch_scatter(pp_handle* h, const uint64_t* ox, const uint64_t* oz, const double* oc,
+                             size_t n, const InputMerge& m, const StepParams& p, int* launches) {
+    *launches += 3;
+    return h->W == 1 ? launch_input<1>(h, ox, oz, oc, n, m, p) : launch_input<2>(h, ox, oz, oc, n, m, p);
 }
 
 NoiseDesc noise_desc(const NoiseHost& nh) {
@@ -1222,9 +1233,14 @@ pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, 
     if (!P.ctr_dev) P.ctr_dev = h->counters;
     const int W = h->W;
 
-    // stage the observable
+    // stage the observable, followed by the input-merge table
     if (n_terms > h->cap) return fail(h, PP_ERR_CAPACITY, "observable larger than capacity");
-    size_t need = std::max<size_t>(n_terms, 1) * (2 * W + 1);
+    if (n_terms > (size_t)INT32_MAX) return fail(h, PP_ERR_ARG, "more than 2^31 - 1 observable terms");
+    for (size_t i = 0; i < n_terms; ++i)
+        if (!(std::fabs(oc[i]) < 4294967296.0))
+            return fail(h, PP_ERR_ARG, "observable coefficient %zu is not finite with magnitude below 2^32", i);
+    const size_t H = input_merge_slots(n_terms);
+    size_t need = std::max<size_t>(n_terms, 1) * (2 * W + 1) + 3 * H;
     if (need > h->stage_cap) {
         if (h->stage) dev_free(h, h->stage);
         h->stage = static_cast<uint64_t*>(dev_alloc(h, need * 8));
@@ -1237,7 +1253,15 @@ pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, 
     uint64_t* sx = h->stage;
     uint64_t* sz = h->stage + n_terms * W;
     double* sc = reinterpret_cast<double*>(h->stage + 2 * n_terms * W);
+    InputMerge im;
+    unsigned char* mt = reinterpret_cast<unsigned char*>(h->stage + std::max<size_t>(n_terms, 1) * (2 * W + 1));
+    im.owner = reinterpret_cast<int*>(mt);
+    im.count = reinterpret_cast<unsigned*>(mt + 4 * H);
+    im.acc = reinterpret_cast<unsigned long long*>(mt + 8 * H);
+    im.hmask = (uint32_t)(H - 1);
     if (n_terms) {
+        CK(cudaMemsetAsync(im.owner, 0xff, 4 * H, h->st));
+        CK(cudaMemsetAsync(im.count, 0, 4 * H + 16 * H, h->st));
         CK(cudaMemcpyAsync(sx, ox, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
         CK(cudaMemcpyAsync(sz, oz, n_terms * W * 8, cudaMemcpyHostToDevice, h->st));
         CK(cudaMemcpyAsync(sc, oc, n_terms * 8, cudaMemcpyHostToDevice, h->st));
@@ -1271,7 +1295,7 @@ pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, 
     p.dB = P.B;
     p.dC = P.C;
     p.next = h->d_subs;
-    if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, p, &P.launches));
+    if (n_terms) CK(dispatch_scatter(h, sx, sz, sc, n_terms, im, p, &P.launches));
     CK(group_spill(h, 0, P.B, P.C, P.ctr_dev, &P.launches));
     CK(cudaMemcpyAsync(P.ctr, P.ctr_dev, sizeof(P.ctr), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));

@@ -864,15 +864,94 @@ __global__ void __launch_bounds__(NWARPS * 32) k_process_global(const StepParams
     }
 }
 
-// Scatters the input observable into the first sub-layer's buckets (the
-// destination layout of p).
+// ----------------------------------------------------------------------------- input merge
+
+// The input observable's duplicate strings are summed before the first
+// sub-layer, exactly and independently of their order: a hash table over the
+// input keys (slot: owner = smallest input index with that key, count, and a
+// 128-bit fixed-point accumulator) collects every duplicated string's
+// coefficients as integers (trunc(c * 2^80)), and the owner carries the total,
+// rounded once to the nearest double, into the first layout.  Strings without
+// duplicates keep their coefficient untouched.
+struct InputMerge {
+    int* owner;                  // [H] smallest input index of the slot's key, -1: empty
+    unsigned* count;             // [H] input strings with the slot's key
+    unsigned long long* acc;     // [2H] 128-bit accumulator (low word, high word)
+    uint32_t hmask;              // H - 1
+};
+
+template <int W>
+__device__ __forceinline__ bool input_key_eq(const uint64_t* ox, const uint64_t* oz, size_t a, size_t b) {
+    bool eq = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) eq = eq && ox[a * W + w] == ox[b * W + w] && oz[a * W + w] == oz[b * W + w];
+    return eq;
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t input_slot0(const uint64_t* ox, const uint64_t* oz, size_t i, uint32_t hmask) {
+    return tile_hash<W>(ox + i * W, oz + i * W, 31) & hmask;
+}
+
+// Slot of input string i's key (after k_input_claim).
+template <int W>
+__device__ __forceinline__ uint32_t input_slot(const uint64_t* ox, const uint64_t* oz, size_t i, const InputMerge& m) {
+    uint32_t h = input_slot0<W>(ox, oz, i, m.hmask);
+    for (uint32_t probe = 0; probe <= m.hmask; ++probe) {
+        const int o = m.owner[h];
+        if (o < 0 || input_key_eq<W>(ox, oz, (size_t)o, i)) return h;
+        h = (h + 1) & m.hmask;
+    }
+    return h;
+}
+
+template <int W>
+__global__ void k_input_claim(const uint64_t* ox, const uint64_t* oz, size_t n, InputMerge m) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t h = input_slot0<W>(ox, oz, i, m.hmask);
+        for (uint32_t probe = 0; probe <= m.hmask; ++probe) {
+            const int prev = atomicCAS(&m.owner[h], -1, (int)i);
+            // a slot's owner only ever moves to a smaller index of the same key
+            if (prev < 0 || input_key_eq<W>(ox, oz, (size_t)prev, i)) {
+                if (prev >= 0) atomicMin(&m.owner[h], (int)i);
+                atomicAdd(&m.count[h], 1u);
+                break;
+            }
+            h = (h + 1) & m.hmask;
+        }
+    }
+}
+
+template <int W>
+__global__ void k_input_accumulate(const uint64_t* ox, const uint64_t* oz, const double* oc, size_t n,
+                                   InputMerge m) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t h = input_slot<W>(ox, oz, i, m);
+        if (m.count[h] < 2) continue;
+        // two's-complement 128-bit addition, split into words with the carry
+        const __int128 v = to_fixed80(oc[i]);
+        const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+        const unsigned long long old = atomicAdd(&m.acc[2 * (size_t)h], lo);
+        atomicAdd(&m.acc[2 * (size_t)h + 1], hi + (old + lo < old ? 1ull : 0ull));
+    }
+}
+
+// Scatters the merged input observable into the first sub-layer's buckets
+// (the destination layout of p): one string per key, from its owner.
 template <int W, typename T>
 __global__ void k_scatter_input(const uint64_t* ox, const uint64_t* oz, const double* oc, size_t n,
-                                StepParams p) {
+                                InputMerge m, StepParams p) {
     const SubLayerDesc& d = *p.next;
     const uint32_t bmask = p.dB - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t h = input_slot<W>(ox, oz, i, m);
+        if (m.owner[h] != (int)i) continue;
+        double c = oc[i];
+        if (m.count[h] > 1) {
+            const unsigned __int128 t = ((unsigned __int128)m.acc[2 * (size_t)h + 1] << 64) | m.acc[2 * (size_t)h];
+            c = fixed80_to_double((__int128)t);
+        }
         uint64_t x[W], z[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -880,7 +959,7 @@ __global__ void k_scatter_input(const uint64_t* ox, const uint64_t* oz, const do
             z[w] = oz[i * W + w];
         }
         uint32_t b = bucket_of<W>(d, x, z, bmask);
-        emit<W, T>(p, b, x, z, T(oc[i]));
+        emit<W, T>(p, b, x, z, T(c));
     }
 }
 

@@ -169,6 +169,38 @@ def test_duplicate_input_strings_are_summed(pp):
     compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), 0.0)
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_duplicate_input_strings_sum_exactly_in_any_order(pp, precision):
+    """Duplicates of one input string are summed exactly whatever their order:
+    1 + 2^-40 - 1 + 2^-40 in any order gives 2^-39, also in the FP32 form,
+    where a float sum in arrival order would lose the small terms.  The
+    circuit is one R_X(0) gate (the identity) with no noise."""
+    zx = np.zeros((1, 1), np.uint64)
+    z0 = np.ones((1, 1), np.uint64)           # Z on qubit 0
+    vals = np.array([1.0, 2.0 ** -40, -1.0, 2.0 ** -40])
+    rng = np.random.default_rng(5)
+    for perm in [np.arange(4), np.array([2, 1, 0, 3]), rng.permutation(4), rng.permutation(4)]:
+        h = pp.Handle(2, precision=precision)
+        h.pp_load_circuit(np.array([[1]], np.uint64), zx, np.array([0.0]), np.array([0], np.int32), 1)
+        h.pp_propagate(np.repeat(zx, 4, 0), np.repeat(z0, 4, 0), vals[perm], 0.0, -1)
+        assert h.pp_expect() == 2.0 ** -39
+        x, z, c = h.pp_export_terms()
+        assert len(c) == 1 and c[0] == 2.0 ** -39
+        h.close()
+
+
+def test_observable_coefficients_must_be_finite_and_below_2_32(pp):
+    h = pp.Handle(2)
+    zx = np.zeros((1, 1), np.uint64)
+    h.pp_load_circuit(np.array([[1]], np.uint64), zx, np.array([0.3]), np.array([0], np.int32), 1)
+    for bad in (np.nan, np.inf, 2.0 ** 32):
+        with pytest.raises(pp.PPError):
+            h.pp_propagate(zx, np.ones((1, 1), np.uint64), np.array([bad]), 0.0, -1)
+    h.pp_propagate(zx, np.ones((1, 1), np.uint64), np.array([2.0 ** 31]), 0.0, -1)
+    assert abs(h.pp_expect() - 2.0 ** 31 * np.cos(0.3)) <= 1e-6
+    h.close()
+
+
 # ----------------------------------------------------------------- every processing tier
 
 TIER_CASES = {"6x6_s3": lambda: inputs.workload_6x6(steps=3, eps=1e-5),
