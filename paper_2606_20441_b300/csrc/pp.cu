@@ -1299,6 +1299,7 @@ pp_status prop_begin(Prop& P, pp_handle* h, size_t n_terms, const uint64_t* ox, 
     CK(group_spill(h, 0, P.B, P.C, P.ctr_dev, &P.launches));
     CK(cudaMemcpyAsync(P.ctr, P.ctr_dev, sizeof(P.ctr), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    if (P.ctr[CTR_DEBUG]) return fail(h, PP_ERR_CUDA, "device bounds check %llu failed", P.ctr[CTR_DEBUG]);
     if (P.ctr[CTR_ERR_REGION]) return fail(h, PP_ERR_CAPACITY, "input overflowed the overflow area");
     P.n_over_in = P.ctr[CTR_SPILL_TOTAL];
     P.N = P.peak = n_terms;
@@ -1391,6 +1392,8 @@ pp_status prop_finish(Prop& P) {
     const bool fin = d.final_ != 0;
     const unsigned long long* ctr = P.ctr;
     if (h->cancel_gen.load() == P.gen) return fail(h, PP_ERR_TIMEOUT, "cancelled after sub-layer %d", s);
+    if (ctr[CTR_DEBUG])
+        return fail(h, PP_ERR_CUDA, "sub-layer %d: device bounds check %llu failed", s, ctr[CTR_DEBUG]);
     for (int tier = 0; tier < N_TIERS; ++tier) {
         P.stats.tier_ms[tier] += P.ms[tier];
         P.stats.tier_strings[tier] += (double)ctr[CTR_LOADED + tier] + (double)ctr[CTR_EMITTED + tier];

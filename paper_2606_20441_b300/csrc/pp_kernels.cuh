@@ -83,8 +83,26 @@ enum {
     CTR_UPDATES = CTR_PHASE_CTA + 4,        // canonical work count of the completed buckets (string lifetimes)
     CTR_STAT,            // tier-0 work statistics when tracing (8): buckets, rounds,
                          // list chunks, listed strings, live pairs, created, revived, 0
-    CTR_COUNT = CTR_STAT + 8
+    CTR_DEBUG = CTR_STAT + 8,   // debug builds: the first failed bounds check (site number)
+    CTR_COUNT
 };
+
+// Bounds checks of the debug build (compiled with PP_DEBUG).  PP_OOB(ok, site,
+// counters) is true when the check fails: it records the first failing site in
+// counters[CTR_DEBUG] and the caller skips the access (no trap, no fault); the
+// host turns a recorded site into an error.  In other builds it is false and
+// costs nothing.  Sites: 1 load source, 2 tile entry, 3 active list, 4 gate
+// index, 5 destination region, 6 overflow area, 7 compact result, 8 bucket
+// index, 9 global-tier slice.
+#ifdef PP_DEBUG
+__device__ __forceinline__ bool pp_oob(bool ok, int site, unsigned long long* counters) {
+    if (!ok) atomicCAS(&counters[CTR_DEBUG], 0ull, (unsigned long long)site);
+    return !ok;
+}
+#define PP_OOB(ok, site, counters) pp_oob((ok), (site), (counters))
+#else
+#define PP_OOB(ok, site, counters) false
+#endif
 
 // Number of work items (buckets) of a tier launch.
 __device__ __forceinline__ uint32_t work_items(const StepParams& p) {
@@ -141,7 +159,8 @@ struct Tile {
     int* n;           // entries used
     int* flag;        // nonzero (a FAIL_* reason): the bucket goes to the next tier
     int* live;
-    int* nact;        // [2] lengths of the two active lists
+    int* nact;        // [3] lengths of the active lists (rotating counter slots)
+    unsigned long long* ctr;   // the launch's counters (debug bounds checks)
     __device__ __forceinline__ T* cbuf(int k) const { return k ? c1 : c; }
 };
 
@@ -318,7 +337,8 @@ __device__ __forceinline__ void act_append(const Tile<W, T, I>& t, int which, in
     int base = 0;
     if (lane == leader) base = atomicAdd(&t.nact[counter], __popc(msk));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (want) t.act[(size_t)which * t.cap + base + __popc(msk & ((1u << lane) - 1u))] = (I)i;
+    const int pos = base + __popc(msk & ((1u << lane) - 1u));
+    if (want && !PP_OOB(pos < t.cap, 3, t.ctr)) t.act[(size_t)which * t.cap + pos] = (I)i;
 }
 
 template <typename T>
@@ -336,8 +356,10 @@ __device__ __forceinline__ float eps_of<float>(const StepParams& p) { return p.e
 template <int W, typename T>
 __device__ __forceinline__ void emit_at(const StepParams& p, uint32_t nb, uint32_t slot, const uint64_t* x,
                                         const uint64_t* z, T c) {
+    if (PP_OOB(nb < p.dB, 8, p.counters)) return;
     if ((uint64_t)slot < p.dC) {
         size_t pos = (size_t)nb * p.dC + slot;
+        if (PP_OOB(pos < p.dcap, 5, p.counters)) return;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             p.dx[(size_t)w * p.dcap + pos] = x[w];
@@ -352,6 +374,7 @@ __device__ __forceinline__ void emit_at(const StepParams& p, uint32_t nb, uint32
         unsigned long long k = atomicAdd(&p.spill_ctr[shard], 1ull);
         if (k >= shard_cap) continue;
         k += (unsigned long long)shard * shard_cap;
+        if (PP_OOB(k < p.rpcap, 6, p.counters)) return;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             p.rpx[(size_t)w * p.rpcap + k] = x[w];
@@ -461,6 +484,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
         const uint64_t* az = reg ? p.sz : p.spz;
         const size_t acap = reg ? p.scap : p.spcap;
         const T* ac = static_cast<const T*>(reg ? p.sc : p.spc);
+        if (PP_OOB(src < acap && i < t.cap, 1, p.counters)) continue;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             if (kAsync) {
@@ -583,6 +607,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                         gm[w] &= gm[w] - 1;
                     }
                 }
+                if (PP_OOB(gg >= 0, 4, t.ctr)) gg = 0;
                 bool more = false;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -596,6 +621,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                 // prologue before any gate), and is never created
                 const bool reach = p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max;
                 if (reach) j = tile_lookup_at<W, T, I>(t, qx, qz, &hslot);
+                if (PP_OOB(j < *t.n, 2, t.ctr)) j = -1;
                 // i R P = phi Q: sign of P's sin-branch into its partner Q
                 const int phi = branch_negative<W, T>(tab, gg, x, z) ? -1 : 1;
                 const T cs = tab.cs[gg], sn = tab.sn[gg];
@@ -748,6 +774,7 @@ __host__ __device__ constexpr size_t tile_layout_bytes(size_t cap) {
 template <int W, typename T, typename I>
 __device__ __forceinline__ Tile<W, T, I> carve_tile(unsigned char* mem, int cap, int* ctl) {
     Tile<W, T, I> t;
+    t.ctr = nullptr;
     t.cap = cap;
     t.hcap = (int)tile_hcap((size_t)cap);
     t.hbits = 31 - __clz(t.hcap);
@@ -802,6 +829,7 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 4 : 1) k_process(const StepPara
     __shared__ StepParams p;
     if (!load_params(p, p0, ps)) return;
     Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem, cap, ctl);
+    t.ctr = p.counters;
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
     if (threadIdx.x == (NT > 32 ? 32 : 0) && p.next) make_act(*p.next, s_adn);
     load_gate_table<W, T>(tab, *p.desc);
@@ -846,6 +874,7 @@ __global__ void __launch_bounds__(NWARPS * 32) k_process_global(const StepParams
     (void)slice_bytes;
     (void)cap;
     Tile<W, T, int32_t> t = carve_tile<W, T, int32_t>(base + p.gslice * blockIdx.x, p.gcap, ctl);
+    t.ctr = p.counters;
     if (threadIdx.x == 0) make_act(*p.desc, s_ad);
     if (threadIdx.x == 32 && p.next) make_act(*p.next, s_adn);
     load_gate_table<W, T>(tab, *p.desc);

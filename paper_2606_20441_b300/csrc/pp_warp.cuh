@@ -71,6 +71,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         const uint64_t* ax = reg ? p.sx : p.spx;
         const uint64_t* az = reg ? p.sz : p.spz;
         const size_t acap = reg ? p.scap : p.spcap;
+        if (PP_OOB(src < acap && i < t.cap, 1, p.counters)) continue;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             cp_async8(&t.x[(size_t)w * t.cap + i], &ax[(size_t)w * acap + src]);
@@ -137,7 +138,8 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
         }
         live += __popc(__ballot_sync(FULL, alive));
         const unsigned am = __ballot_sync(FULL, has_gates);
-        if (has_gates) t.act[na + __popc(am & lt)] = (int16_t)i;
+        if (has_gates && !PP_OOB(na + __popc(am & lt) < t.cap, 3, p.counters))
+            t.act[na + __popc(am & lt)] = (int16_t)i;
         na += __popc(am);
     }
     __syncwarp();
@@ -185,6 +187,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                         gm[w] &= gm[w] - 1;
                     }
                 }
+                if (PP_OOB(gg >= 0, 4, p.counters)) gg = 0;
                 bool more = false;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -198,6 +201,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 // prologue before any gate), and is never created
                 const bool reach = p.w_max < 0 || weight_of<W>(qx, qz) <= p.w_max;
                 if (reach) j = tile_lookup_at<W, T, int16_t>(t, qx, qz, &hslot);
+                if (PP_OOB(j < n, 2, p.counters)) j = -1;
                 // i R P = phi Q: sign of P's sin-branch into its partner Q
                 const int phi = branch_negative<W, T>(tab, gg, x, z) ? -1 : 1;
                 const T cs = tab.cs[gg], sn = tab.sn[gg];
@@ -275,9 +279,9 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
             }
             const unsigned km = __ballot_sync(FULL, keep);
             const unsigned jm = __ballot_sync(FULL, join);
-            if (keep) Ln[nn + __popc(km & lt)] = (int16_t)i;
+            if (keep && !PP_OOB(nn + __popc(km & lt) < t.cap, 3, p.counters)) Ln[nn + __popc(km & lt)] = (int16_t)i;
             nn += __popc(km);
-            if (join) Ln[nn + __popc(jm & lt)] = (int16_t)idx;
+            if (join && !PP_OOB(nn + __popc(jm & lt) < t.cap, 3, p.counters)) Ln[nn + __popc(jm & lt)] = (int16_t)idx;
             nn += __popc(jm);
         }
         __syncwarp();
@@ -379,6 +383,7 @@ __global__ void __launch_bounds__(32 * NW, PP_WARP_MIN_BLOCKS) k_process_warp(co
     __syncthreads();
 
     Tile<W, T, int16_t> t = carve_tile<W, T, int16_t>(smem + warp_tile_bytes<W, T>(cap) * wid, cap, s_ctl[wid]);
+    t.ctr = p.counters;
     WarpAcc acc{0ull, 0ull, 0ull};
     unsigned long long upd = 0;
     const uint32_t n_items = work_items(p);

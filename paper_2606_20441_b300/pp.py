@@ -91,11 +91,14 @@ NOALLOC_MAX_TERMS = 1 << 27
 _lib = None
 
 
-def load_library(path: str = LIB_PATH):
-    """Loads libpp.so (raises OSError if it was not built)."""
+def load_library(path: Optional[str] = None):
+    """Loads libpp.so (raises OSError if it was not built).  The environment
+    variable PP_LIBRARY selects another build of the library, e.g. the debug
+    build (build.DEBUG_LIB) with device bounds checks."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("PP_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise OSError("libpp.so not built at %s (run paper_2606_20441_b300.build.build())" % path)
     L = ctypes.CDLL(path)
