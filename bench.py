@@ -41,9 +41,9 @@ from paper_2606_20441_b300 import inputs  # noqa: E402
 
 METRIC = "Pauli-term updates/s"
 UNIT = "updates/s"
-PROFILE = os.path.join(ROOT, "profiles", "k_process_orbit_tfim7x8.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_process_warp_tfim7x8.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2606_20441_b300", "csrc", f)
-                  for f in ("pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh", "pp_orbit.cuh")]
+                  for f in ("pp_device.cuh", "pp_kernels.cuh", "pp_warp.cuh")]
 
 
 def workload(args):
@@ -417,10 +417,10 @@ def ours_arm(args, rank, world, local_rank):
     main_ms_avg = tier_ms[0] / max(1, tier_launches[0])
     main_bytes = tier_strings[0] * bps / max(1, tier_launches[0])
     achieved = main_bytes / (main_ms_avg / 1000.0) / 1e9 if main_ms_avg > 0 else 0.0
-    roofline = {"bound": "hbm", "limiter": "latency: issue slots and memory latency, not DRAM bandwidth "
-                "(profiles/k_process_orbit_tfim7x8.md)",
-                "kernel": "k_process_orbit (tier 0: one warp per bucket, strings grouped by orbit into dense "
-                          "coefficient blocks)",
+    roofline = {"bound": "hbm", "limiter": "instruction issue and shared-memory latency of the gate rounds, "
+                "not DRAM bandwidth (profiles/k_process_warp_tfim7x8.md)",
+                "kernel": "k_process_warp<1, float, 4> (tier 0: one warp per bucket, 248-string tiles in shared "
+                          "memory, 4 warps per CTA)",
                 "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": main_bytes, "avg_launch_ms": main_ms_avg,

@@ -40,20 +40,23 @@ struct TierCfg {
     int threads;
     int cap1;     // tile entries for W = 1
     int cap2;     // tile entries for W = 2
+    int load;     // largest bucket taken, in 1/100 of the tile: the rest of the tile
+                  // holds the strings the gates create (a bucket that outgrows it
+                  // anyway is passed on, its work lost)
 };
-#ifndef PP_TIER1_THREADS
-#define PP_TIER1_THREADS 64
+#ifndef PP_CTA_TILE1_THREADS
+#define PP_CTA_TILE1_THREADS 64
 #endif
 constexpr int WARP_TILE_WARPS2 = 2;   // warps per CTA of the second warp tier
-#ifndef PP_TIER2_THREADS
-#define PP_TIER2_THREADS 256
+#ifndef PP_CTA_TILE2_THREADS
+#define PP_CTA_TILE2_THREADS 256
 #endif
 constexpr TierCfg kTiers[N_TIERS] = {
-    {32 * WARP_TILE_WARPS, 248, 248},   // one warp per bucket, 4 warps per CTA
-    {32 * WARP_TILE_WARPS2, 512, 384},  // one warp per bucket, larger tiles, 2 warps per CTA
-    {PP_TIER1_THREADS, 1024, 1024},     // CTA tiles: few warps, so that a round's
-    {PP_TIER2_THREADS, 4096, 2048},     // barriers wait on few warps
-    {512, 1 << 20, 1 << 20}};           // global-memory tile
+    {32 * WARP_TILE_WARPS, 248, 248, 60},   // one warp per bucket, 4 warps per CTA
+    {32 * WARP_TILE_WARPS2, 512, 384, 60},  // one warp per bucket, larger tiles, 2 warps per CTA
+    {PP_CTA_TILE1_THREADS, 1024, 1024, 75},     // CTA tiles: few warps, so that a round's
+    {PP_CTA_TILE2_THREADS, 4096, 2048, 75},     // barriers wait on few warps
+    {512, 1 << 20, 1 << 20, 75}};           // global-memory tile
 constexpr int kGlobalTier = N_TIERS - 1;
 constexpr int kFallbackCTAs = 16; // CTAs of the global tier
 constexpr int kFallbackCap = 1 << 20;
@@ -1375,7 +1378,7 @@ bool prop_tier(Prop& P, int tier, uint32_t* n_items) {
     p.work_ctr = CTR_WORK + tier;
     p.defer_ctr = CTR_DEFER + (tier < kGlobalTier ? tier : 0);
     const bool orbit = tier == 0 && P.use_orbit(P.s);
-    p.max_load = (uint32_t)((tier == kGlobalTier ? h->fb_cap : tier_cap(h, tier)) * 3 / 4);
+    p.max_load = (uint32_t)((size_t)(tier == kGlobalTier ? h->fb_cap : tier_cap(h, tier)) * kTiers[tier].load / 100);
     if (orbit) p.max_load = (uint32_t)orbit_load_cap(h);
     if (tier < h->tune.first_tier) p.max_load = 0;   // every bucket is passed on
     if (orbit) P.stats.orbit_launches++;
