@@ -257,6 +257,12 @@ const char* pp_last_error(const pp_handle* h);
  *                    coefficient blocks); 0 (default): every sub-layer uses
  *                    the sparse (hashed) warp tiles and same-signature gates
  *                    fuse across up to four ascending segments.
+ *   tile_cap         strings per tile of tiers 0..3 (the two warp tiers, the
+ *                    two CTA tiers); 0 = library default (248, 512, 1024, 4096
+ *                    for W = 1; 248, 384, 1024, 2048 for W = 2); else 64..8192,
+ *                    and the tier's tiles must fit the device's shared memory
+ *                    per CTA.  A bucket that outgrows a tile moves to the next
+ *                    tier, so every choice gives the same result.
  * pp_set_tuning copies *t and takes effect at the next pp_propagate.
  * Errors: PP_ERR_ARG (NULL pointer, value out of range; the handle keeps its
  * previous tuning).  pp_get_tuning writes the values in effect (defaults
@@ -266,6 +272,7 @@ typedef struct {
     double bucket_headroom;
     int first_tier;
     int orbit_tiles;
+    int tile_cap[4];
 } pp_tuning;
 
 pp_status pp_set_tuning(pp_handle* h, const pp_tuning* t);

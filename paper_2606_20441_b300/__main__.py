@@ -40,13 +40,15 @@ def main(argv=None) -> int:
     r.add_argument("--headroom", type=float, default=0.0, help="pp_set_tuning bucket_headroom (0: default)")
     r.add_argument("--first-tier", type=int, default=0, help="pp_set_tuning first_tier (0: default)")
     r.add_argument("--orbit-tiles", action="store_true", help="pp_set_tuning orbit_tiles: orbit tiles in tier 0")
+    r.add_argument("--tile-caps", default="0,0,0,0", help="pp_set_tuning tile_cap of tiers 0-3 (0: default)")
     a = ap.parse_args(argv)
 
     from . import pp
     inst = _instance(a.workload, a.eps, a.steps, a.w_max)
     h = pp.Handle(inst.n_qubits, precision=a.precision, max_terms=a.max_terms, timing=True)
     h.load_instance(inst)
-    h.pp_set_tuning(a.fused_gates, a.headroom, a.first_tier, int(a.orbit_tiles))
+    h.pp_set_tuning(a.fused_gates, a.headroom, a.first_tier, int(a.orbit_tiles),
+                    tile_caps=[int(v) for v in a.tile_caps.split(",")])
     for _ in range(a.repeat):
         h.run_instance(inst)
     e = h.pp_expect()
@@ -57,7 +59,7 @@ def main(argv=None) -> int:
                       "tier_strings": list(s.tier_strings), "bytes_per_string": s.bytes_per_string,
                       "kernel_launches": s.kernel_launches, "orbit_launches": s.orbit_launches,
                       "seconds": s.seconds,
-                      "tuning": list(h.pp_get_tuning())}), flush=True)
+                      "tuning": h.tuning()}), flush=True)
     h.close()
     return 0
 

@@ -1,11 +1,12 @@
-"""Autotuner for the sub-layer plan (pp_set_tuning).
+"""Autotuner for the sub-layer plan and the tile sizes (pp_set_tuning).
 
-Two knobs shape a propagation's kernels: how many commuting gates are fused
+Three knobs shape a propagation's kernels: how many commuting gates are fused
 into one sub-layer (fewer passes over the strings, but orbits of up to
-2^gates strings per bucket, which push buckets into the slower CTA tiers), and
-the bucket headroom (how full a warp tile a bucket is planned to be, i.e. how
-many buckets a sub-layer's strings are hashed into).  The best pair depends on
-lattice size, depth, threshold and weight cap.
+2^gates strings per bucket, which push buckets into the slower tiers), the
+bucket headroom (how full a warp tile a bucket is planned to be, i.e. how many
+buckets a sub-layer's strings are hashed into), and the tile sizes of the two
+warp tiers (larger tiles hold larger buckets but leave fewer warps resident).
+The best setting depends on lattice size, depth, threshold and weight cap.
 
 Every setting gives the same result, bit for bit: each plan reproduces
 gate-by-gate propagation with truncation after every gate.  So tuning can run
@@ -22,10 +23,23 @@ import math
 import threading
 from typing import Dict, List, Optional, Sequence, Tuple
 
-Setting = Tuple[int, float]   # (max_fused_gates, bucket_headroom)
+# (max_fused_gates, bucket_headroom) or (max_fused_gates, bucket_headroom,
+# tier-0 tile, tier-1 tile); zeros select the library defaults
+Setting = Tuple
 
-# (0, 0.0) is the library default (whole layers, headroom 2.0)
-CANDIDATES: List[Setting] = [(0, 0.0), (32, 2.4), (16, 1.6), (64, 1.6), (32, 2.0), (64, 2.8)]
+# (0, 0.0) is the library default (whole layers, headroom 2.0, tiles 248 and 512)
+CANDIDATES: List[Setting] = [(0, 0.0), (32, 2.4), (16, 1.6), (64, 1.6), (0, 0.0, 200, 448), (0, 0.0, 320, 640)]
+
+
+def _setting(v) -> Setting:
+    """A setting from its stored form (numbers or strings)."""
+    return tuple([int(float(v[0])), float(v[1])] + [int(float(a)) for a in v[2:]])
+
+
+def set_tuning(handle, setting: Setting):
+    """Applies a setting to a handle (tile sizes 0 = library default)."""
+    caps = tuple(setting[2:4]) + (0,) * (4 - len(setting[2:4]))
+    handle.pp_set_tuning(setting[0], setting[1], tile_caps=caps)
 
 
 def class_key(inst) -> str:
@@ -77,7 +91,7 @@ class Tuner:
     def apply(self, handle, inst) -> Setting:
         """Sets the handle's tuning for this instance; returns the setting."""
         setting = self.choose(class_key(inst))
-        handle.pp_set_tuning(setting[0], setting[1])
+        set_tuning(handle, setting)
         return setting
 
     def observe(self, inst, setting: Setting, updates: float, seconds: float):
@@ -91,7 +105,7 @@ class Tuner:
         key = class_key(inst)
         handle.load_instance(inst)
         for c in self.candidates:
-            handle.pp_set_tuning(c[0], c[1])
+            set_tuning(handle, c)
             for _ in range(repeats):
                 handle.run_instance(inst)
                 st = handle.pp_get_stats()
@@ -104,18 +118,17 @@ class Tuner:
     def to_json(self) -> str:
         with self._lock:
             return json.dumps({"fixed": {k: list(v) for k, v in self.fixed.items()},
-                               "samples": {k: {"%d,%g" % c: v for c, v in d.items()}
+                               "samples": {k: {",".join("%g" % a for a in c): v for c, v in d.items()}
                                            for k, d in self.samples.items()}})
 
     @classmethod
     def from_json(cls, text: str, candidates: Optional[Sequence[Setting]] = None) -> "Tuner":
         d = json.loads(text)
         t = cls(candidates or CANDIDATES)
-        t.fixed = {k: (int(v[0]), float(v[1])) for k, v in d.get("fixed", {}).items()}
+        t.fixed = {k: _setting(v) for k, v in d.get("fixed", {}).items()}
         for k, m in d.get("samples", {}).items():
             for cs, v in m.items():
-                a, b = cs.split(",")
-                t.samples.setdefault(k, {})[(int(a), float(b))] = list(v)
+                t.samples.setdefault(k, {})[_setting(cs.split(","))] = list(v)
         for k, m in t.samples.items():
             if all(c in m for c in t.candidates):
                 t._handed[k] = len(t.candidates) * t.trials

@@ -95,11 +95,12 @@ struct Arena {
 
 struct pp_handle {
     pp_options opt;
-    pp_tuning tune{0, 0.0, 0, 0};   // zeros select the library defaults
+    pp_tuning tune{0, 0.0, 0, 0, {0, 0, 0, 0}};   // zeros select the library defaults
     int n = 0, W = 1;
     cudaStream_t st = nullptr;
     std::string err;
     int sm_count = 0;
+    size_t smem_optin = 0;           // largest dynamic shared memory a CTA may opt into
     int device = 0;
 
     // circuit
@@ -883,6 +884,7 @@ cudaError_t launch_process(pp_handle* h, const StepParams& p, int tier, bool orb
 // the table for measurements.
 int tier_cap(const pp_handle* h, int tier) {
     int c = h->W == 1 ? kTiers[tier].cap1 : kTiers[tier].cap2;
+    if (tier < kGlobalTier && h->tune.tile_cap[tier] > 0) return h->tune.tile_cap[tier];
     if (tier < kGlobalTier) {
         if (const char* e = getenv("PP_TILE_CAPS")) {
             int v[4] = {0, 0, 0, 0};
@@ -891,6 +893,21 @@ int tier_cap(const pp_handle* h, int tier) {
         }
     }
     return c;
+}
+
+// Dynamic shared memory of one CTA of shared-memory tier `tier` with tiles of
+// `cap` strings, plus a margin for the kernels' static shared memory.
+template <int W, typename T>
+size_t tile_smem_bytes_t(int tier, int cap) {
+    const size_t stat = 16384;
+    if (tier == 0) return warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS + stat;
+    if (tier == 1) return warp_tile_bytes<W, T>((size_t)cap) * WARP_TILE_WARPS2 + stat;
+    return tile_layout_bytes<W, T, int16_t>((size_t)cap) + stat;
+}
+size_t tile_smem_bytes(const pp_handle* h, int tier, int cap) {
+    const bool f32 = h->opt.precision == PP_PRECISION_FP32;
+    if (h->W == 1) return f32 ? tile_smem_bytes_t<1, float>(tier, cap) : tile_smem_bytes_t<1, double>(tier, cap);
+    return f32 ? tile_smem_bytes_t<2, float>(tier, cap) : tile_smem_bytes_t<2, double>(tier, cap);
 }
 
 cudaError_t dispatch_process(pp_handle* h, const StepParams& p, int tier, bool orbit, uint32_t n_items,
@@ -1717,13 +1734,16 @@ pp_status pp_create(const pp_options* opt, int n_qubits, pp_handle** out) {
     h->st = static_cast<cudaStream_t>(h->opt.cuda_stream);
     h->device = 0;
     int dev = 0;
+    int optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return PP_ERR_CUDA;
     }
     h->device = dev;
+    h->smem_optin = (size_t)optin;
     *out = h;
     return PP_OK;
 }
@@ -1751,6 +1771,15 @@ pp_status pp_set_tuning(pp_handle* h, const pp_tuning* t) {
         return fail(h, PP_ERR_ARG, "bucket_headroom must be 0 (default) or in [1, 16]");
     if (t->first_tier < 0 || t->first_tier >= N_TIERS) return fail(h, PP_ERR_ARG, "first_tier must be in 0..4");
     if (t->orbit_tiles != 0 && t->orbit_tiles != 1) return fail(h, PP_ERR_ARG, "orbit_tiles must be 0 or 1");
+    for (int tier = 0; tier < kGlobalTier; ++tier) {
+        const int c = t->tile_cap[tier];
+        if (c == 0) continue;
+        if (c < 64 || c > 8192) return fail(h, PP_ERR_ARG, "tile_cap[%d] must be 0 (default) or 64..8192", tier);
+        const size_t need = tile_smem_bytes(h, tier, c);
+        if (need > h->smem_optin)
+            return fail(h, PP_ERR_ARG, "tile_cap[%d] = %d needs %zu bytes of shared memory per CTA (device: %zu)",
+                        tier, c, need, h->smem_optin);
+    }
     if (t->max_fused_gates != h->tune.max_fused_gates || t->orbit_tiles != h->tune.orbit_tiles) h->subs_dirty = true;
     h->tune = *t;
     return PP_OK;
@@ -1776,6 +1805,7 @@ pp_status pp_get_tuning(const pp_handle* h, pp_tuning* t) {
     t->bucket_headroom = bucket_headroom(h);
     t->first_tier = h->tune.first_tier;
     t->orbit_tiles = h->tune.orbit_tiles;
+    for (int tier = 0; tier < kGlobalTier; ++tier) t->tile_cap[tier] = tier_cap(h, tier);
     return PP_OK;
 }
 

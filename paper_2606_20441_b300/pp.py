@@ -73,7 +73,8 @@ class pp_tuning(ctypes.Structure):
     _fields_ = [("max_fused_gates", ctypes.c_int),
                 ("bucket_headroom", ctypes.c_double),
                 ("first_tier", ctypes.c_int),
-                ("orbit_tiles", ctypes.c_int)]
+                ("orbit_tiles", ctypes.c_int),
+                ("tile_cap", ctypes.c_int * 4)]
 
 
 class PPError(RuntimeError):
@@ -254,8 +255,9 @@ class Handle:
         return s
 
     def pp_set_tuning(self, max_fused_gates: int = 0, bucket_headroom: float = 0.0, first_tier: int = 0,
-                      orbit_tiles: int = 0):
-        t = pp_tuning(int(max_fused_gates), float(bucket_headroom), int(first_tier), int(orbit_tiles))
+                      orbit_tiles: int = 0, tile_caps=(0, 0, 0, 0)):
+        caps = (ctypes.c_int * 4)(*[int(c) for c in tuple(tile_caps) + (0,) * (4 - len(tile_caps))])
+        t = pp_tuning(int(max_fused_gates), float(bucket_headroom), int(first_tier), int(orbit_tiles), caps)
         self._check(self.L.pp_set_tuning(self.h, ctypes.byref(t)))
 
     def pp_get_tuning(self):
@@ -268,7 +270,9 @@ class Handle:
         """Every tuning field in effect."""
         t = pp_tuning()
         self._check(self.L.pp_get_tuning(self.h, ctypes.byref(t)))
-        return {f: getattr(t, f) for f, _ in pp_tuning._fields_}
+        d = {f: getattr(t, f) for f, _ in pp_tuning._fields_}
+        d["tile_cap"] = list(d["tile_cap"])
+        return d
 
     # convenience: a whole Instance
     def load_instance(self, inst: "inputs.Instance"):

@@ -8,13 +8,13 @@ class FakeHandle:
     def __init__(self):
         self.tuning = None
 
-    def pp_set_tuning(self, g, h):
-        self.tuning = (g, h)
+    def pp_set_tuning(self, g, h, tile_caps=(0, 0, 0, 0)):
+        self.tuning = (g, h) + tuple(c for c in tile_caps[:2] if c)
 
 
 def test_explore_then_exploit_per_class():
-    cands = [(16, 1.6), (8, 1.6), (32, 2.0)]
-    speed = {(16, 1.6): 5.0, (8, 1.6): 3.0, (32, 2.0): 9.0}
+    cands = [(16, 1.6), (8, 1.6), (32, 2.0), (0, 0.0, 200, 448)]
+    speed = {(16, 1.6): 5.0, (8, 1.6): 3.0, (32, 2.0): 9.0, (0, 0.0, 200, 448): 7.0}
     t = autotune.Tuner(cands, trials=2)
     rng = inputs.SplitMix64(7)
     a = inputs.random_tfim(rng, "a", 4, 4, 5, 5, 1e-4, w_max=8)
@@ -35,6 +35,7 @@ def test_explore_then_exploit_per_class():
     t2 = autotune.Tuner.from_json(t.to_json(), cands)
     assert t2.best(autotune.class_key(a)) == (32, 2.0)
     assert t2.choose(autotune.class_key(a)) == (32, 2.0)
+    assert t2.samples[autotune.class_key(a)][(0, 0.0, 200, 448)] == [7.0e9, 7.0e9]
 
 
 def test_failed_runs_are_not_scored():

@@ -59,3 +59,26 @@ def test_served_results_equal_alone(pp):
         e_ref, n_ref = alone(pp, r.instance, 32)
         assert o.terms == n_ref
         assert o.expect == e_ref
+
+
+def test_served_fp64_results_against_oracle(pp):
+    """A request stream served in FP64 (continuous batching, the autotuner
+    varying plans and tile sizes from request to request): every result matches
+    the CPU oracle, to the exact expectation's tolerance and the same term
+    count."""
+    from oracle import oracle
+    from paper_2606_20441_b300 import autotune, serving
+    from tests.parity import expect_tol
+    reqs = inputs.workload_serving(count=8, rate_hz=100.0, seed=inputs.SEED_BASE + 50, side_hi=5, steps_hi=6,
+                                   eps_set=(1e-3,), w_max=6)
+    ex = serving.GpuExecutor(n_small=3, hbm_budget_bytes=2e9, precision=64, n_large=1,
+                             large_fraction=0.5, tuner=autotune.Tuner())
+    try:
+        out = serving.Server(ex, n_workers=3, n_large=1).serve(reqs)
+    finally:
+        ex.close()
+    assert all(o.status == pp.PP_OK for o in out), [(o.rid, o.status) for o in out]
+    for o, r in zip(out, sorted(reqs, key=lambda r: r.rid)):
+        ref = oracle.run(r.instance)
+        assert abs(o.expect - ref.expect) <= expect_tol((ref.x, ref.z, ref.c)), (r.rid, o.expect, ref.expect)
+        assert o.terms == len(ref.c), (r.rid, o.terms, len(ref.c))

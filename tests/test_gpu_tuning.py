@@ -1,6 +1,7 @@
-"""Plan tuning changes run time only: every (max_fused_gates, bucket_headroom)
-gives the same strings and coefficients, bit for bit, and the same exact
-expectation; out-of-range values are rejected without changing the handle."""
+"""Plan tuning changes run time only: every (max_fused_gates, bucket_headroom,
+tile sizes) gives the same strings and coefficients, bit for bit, and the same
+exact expectation; out-of-range values are rejected without changing the
+handle."""
 import numpy as np
 import pytest
 
@@ -29,8 +30,10 @@ def test_every_setting_gives_identical_results(pp, precision):
     h = pp.Handle(inst.n_qubits, precision=precision, max_terms=40_000_000)
     h.load_instance(inst)
     ref = None
-    for g, hr in [(16, 1.6), (1, 1.6), (4, 1.0), (8, 3.0), (32, 1.6), (64, 16.0), (0, 0.0)]:
-        h.pp_set_tuning(g, hr)
+    for g, hr, caps in [(16, 1.6, ()), (1, 1.6, ()), (4, 1.0, ()), (8, 3.0, ()), (32, 1.6, ()),
+                        (64, 16.0, ()), (0, 0.0, (128, 256, 512, 2048)), (0, 0.0, (400, 800, 2048, 4096)),
+                        (0, 0.0, ())]:
+        h.pp_set_tuning(g, hr, tile_caps=caps)
         h.run_instance(inst)
         got = (h.pp_expect(),) + _sorted_terms(*h.pp_export_terms())
         if ref is None:
@@ -54,6 +57,15 @@ def test_tuning_arguments(pp):
         assert h.pp_get_tuning() == (24, 2.5)
     h.pp_set_tuning(0, 0.0)
     assert h.pp_get_tuning() == (64, 2.0)
+    assert h.tuning()["tile_cap"] == [248, 512, 1024, 4096]
+    h.pp_set_tuning(0, 0.0, tile_caps=(300, 600, 0, 0))
+    assert h.tuning()["tile_cap"] == [300, 600, 1024, 4096]
+    for bad in [(32, 0, 0, 0), (0, 9000, 0, 0), (0, 0, 0, 8192 * 2)]:
+        with pytest.raises(pp.PPError):
+            h.pp_set_tuning(0, 0.0, tile_caps=bad)
+        assert h.tuning()["tile_cap"] == [300, 600, 1024, 4096]
+    with pytest.raises(pp.PPError):   # 4 warp tiles of 8192 strings exceed a CTA's shared memory
+        h.pp_set_tuning(0, 0.0, tile_caps=(8192, 0, 0, 0))
     h.close()
     h2 = pp.Handle(100)
     h2.pp_set_tuning(128, 1.6)
