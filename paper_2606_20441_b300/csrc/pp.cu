@@ -999,7 +999,9 @@ cudaError_t apply_noise(pp_handle* h, const NoiseHost& nh, int side, uint32_t B,
 
 // Groups the overflow strings of a freshly written layout by bucket.  Runs
 // whether or not anything spilled (the kernels find out on the device); the
-// number of grouped strings lands in counters[CTR_SPILL_TOTAL].
+// number of grouped strings lands in counters[CTR_SPILL_TOTAL].  When the
+// sub-layer's output outgrew its layout (it runs again from its input), the
+// strings are not moved: the grouped overflow area still holds the input's.
 cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, unsigned long long* counters,
                         int* launches) {
     cudaError_t e = cudaMemsetAsync(counters + CTR_SPILL_TOTAL, 0, sizeof(unsigned long long), h->st);
@@ -1011,11 +1013,11 @@ cudaError_t group_spill(pp_handle* h, int side, uint32_t nB, uint64_t C, unsigne
     const Arena& r = h->spill_raw;
     const Arena& o = h->spill_grp;
     if (h->W == 1) {
-        if (f32) k_spill_move<1, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
-        else k_spill_move<1, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
+        if (f32) k_spill_move<1, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap, counters, h->cap);
+        else k_spill_move<1, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap, counters, h->cap);
     } else {
-        if (f32) k_spill_move<2, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap);
-        else k_spill_move<2, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap);
+        if (f32) k_spill_move<2, float><<<g2, 256, 0, h->st>>>(r.x, r.z, (const float*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (float*)o.c, h->spill_cap, counters, h->cap);
+        else k_spill_move<2, double><<<g2, 256, 0, h->st>>>(r.x, r.z, (const double*)r.c, h->spill_b, h->spill_s, h->spill_cap, h->spill_ctr, h->soff[side], o.x, o.z, (double*)o.c, h->spill_cap, counters, h->cap);
     }
     *launches += 2;
     return cudaGetLastError();
@@ -1621,6 +1623,8 @@ void run_lockstep(pp_handle* const* handles, const pp_batch_item* items, const s
             g.C = P.nC;
             g.soff = hk->soff[P.side ^ 1];
             g.total = P.ctr_dev + CTR_SPILL_TOTAL;
+            g.ctr = P.ctr_dev;
+            g.dcap = hk->cap;
             g.rx = hk->spill_raw.x;
             g.rz = hk->spill_raw.z;
             g.rc = hk->spill_raw.c;

@@ -992,6 +992,14 @@ __global__ void k_scatter_input(const uint64_t* ox, const uint64_t* oz, const do
     }
 }
 
+// Whether a sub-layer's output outgrew its layout (strings lost to a full
+// overflow area, or more strings than the capacity): the sub-layer then runs
+// again from its input, whose grouped overflow strings share the grouped
+// overflow area with the output's, so the output's must not be grouped.
+__device__ __forceinline__ bool spill_outgrown(const unsigned long long* ctr, uint64_t dcap) {
+    return ctr && (ctr[CTR_ERR_REGION] != 0 || ctr[CTR_OUT] > dcap);
+}
+
 // Arguments of the overflow grouping of one layout (batched launches take an
 // array, one per grid row / slice).
 struct SpillArgs {
@@ -1011,6 +1019,8 @@ struct SpillArgs {
     uint64_t* oz;
     void* oc;
     uint64_t ocap;
+    const unsigned long long* ctr;   // the sub-layer's counters (see spill_outgrown)
+    uint64_t dcap;                   // capacity of the destination layout
     // zeroing at the start of a sub-layer (k_clear): the destination fill
     // counters [0, zero_n), the overflow shard counters, and the counters
     uint32_t* zero_fill;
@@ -1083,6 +1093,7 @@ __global__ void k_spill_offsets_batch(const SpillArgs* a) {
 template <int W, typename T>
 __global__ void k_spill_move_batch(const SpillArgs* a) {
     const SpillArgs& s = a[blockIdx.z];
+    if (spill_outgrown(s.ctr, s.dcap)) return;
     const uint64_t shard_cap = s.rcap / NSPILL;
     const uint64_t sh = blockIdx.x;
     const uint64_t fill = s.shard_fill[sh] < shard_cap ? s.shard_fill[sh] : shard_cap;
@@ -1104,7 +1115,9 @@ __global__ void k_spill_move_batch(const SpillArgs* a) {
 template <int W, typename T>
 __global__ void k_spill_move(const uint64_t* rx, const uint64_t* rz, const T* rc, const uint32_t* rb,
                              const uint32_t* rs, uint64_t rcap, const unsigned long long* shard_fill,
-                             const uint64_t* soff, uint64_t* ox, uint64_t* oz, T* oc, uint64_t ocap) {
+                             const uint64_t* soff, uint64_t* ox, uint64_t* oz, T* oc, uint64_t ocap,
+                             const unsigned long long* ctr, uint64_t dcap) {
+    if (spill_outgrown(ctr, dcap)) return;
     const uint64_t shard_cap = rcap / NSPILL;
     const uint64_t s = blockIdx.x;
     const uint64_t fill = shard_fill[s] < shard_cap ? shard_fill[s] : shard_cap;

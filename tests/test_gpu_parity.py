@@ -396,3 +396,33 @@ def test_expectation_is_the_correctly_rounded_exact_sum(pp):
     exact = float(sum(Fraction(c) for letters, c in terms if all(v == "Z" for v in letters.values())))
     assert exact == 1.0 + 2.0 ** -52
     assert got.expect == exact
+
+
+def _last_layers(inst, k):
+    """The instance restricted to its last k layers in time (the first k
+    layers of the backward pass)."""
+    import dataclasses
+    lo = inst.n_layers - k
+    keep = inst.layer_of >= lo
+    noise = [dataclasses.replace(m, layer=m.layer - lo) for m in inst.noise if m.layer >= lo]
+    return dataclasses.replace(inst, gate_x=inst.gate_x[keep], gate_z=inst.gate_z[keep], theta=inst.theta[keep],
+                               layer_of=(inst.layer_of[keep] - lo).astype(np.int32), n_layers=k, noise=noise)
+
+
+def test_sub_layer_rerun_keeps_its_input(pp):
+    """Early sub-layers of this 7x8 instance grow its strings ~10x, far past
+    the planner's estimate: the sixth sub-layer outgrows the capacity and runs
+    again from its input after the buffers grow, and that input has strings in
+    the grouped overflow area, which the failed attempt must leave untouched.
+    The result matches the oracle, twice in a row (runs are deterministic)."""
+    import dataclasses
+    inst = [i for i in inputs.workload_batch64(eps=1e-6) if i.name == "batch37"][0]
+    cut = dataclasses.replace(_last_layers(inst, 5), eps=1e-6, w_max=10)
+    ref = oracle.run(cut)
+    runs = [pp.propagate(cut) for _ in range(2)]
+    for got in runs:
+        assert got.stats.retries > 0
+        compare_terms((got.x, got.z, got.c), (ref.x, ref.z, ref.c), cut.eps)
+        assert abs(got.expect - ref.expect) <= expect_tol((ref.x, ref.z, ref.c))
+        assert got.stats.updates == ref.updates
+    assert np.array_equal(runs[0].c, runs[1].c)
