@@ -465,6 +465,9 @@ def pool_arm(args, rank, world, local_rank):
     from paper_2606_20441_b300 import autotune, build, pp, serving
     torch.cuda.set_device(local_rank)
     build.build()
+    # the tightest setting at which every instance fits its worker's share of
+    # the GPU within seconds (without a weight cap, some instances of the batch
+    # outgrow a worker's share and run for tens of seconds)
     eps, w_max = 1e-4, 8
     if args.workers <= 0:
         args.workers = 8 if args.workload == "batch64" else 12
@@ -520,6 +523,26 @@ def pool_arm(args, rank, world, local_rank):
             h.close()
         return (upd / secs if secs > 0 else None), res
 
+    # the batch's instances once more as one lockstep batch (pp_propagate_batch:
+    # every instance advances one fused sub-layer per step and each kernel is
+    # launched once per step for all of them), FP32
+    lockstep = None
+    if args.workload == "batch64":
+        hs = [pp.Handle(i.n_qubits, precision=args.precision) for i in insts]
+        for h, i in zip(hs, insts):
+            h.load_instance(i)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st = pp.pp_propagate_batch(hs, insts, eps=eps, w_max=w_max)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t
+        upd = sum(h.pp_get_stats().updates for h, x in zip(hs, st) if x == pp.PP_OK)
+        lockstep = {"updates_per_s": upd / sec, "seconds": sec,
+                    "completed": sum(1 for x in st if x == pp.PP_OK), "instances": len(insts)}
+        for h in hs:
+            h.close()
+        torch.cuda.empty_cache()
+
     single64 = single32 = None
     errs = []
     if not args.no_single:
@@ -541,6 +564,7 @@ def pool_arm(args, rank, world, local_rank):
             "config": cfg, "served": summ["served"], "failed": summ["failed"],
             "escalated": summ["escalated"], "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
             "single_instance_fp64_updates_per_s": single64, "single_instance_fp32_updates_per_s": single32,
+            "lockstep": lockstep,
             "fp32_vs_fp64_abs_err": ({"max": max(errs), "median": statistics.median(errs)} if errs else None),
             "compared": len(errs), "cpu_baseline": cpu,
             "tuned": {k: list(tuner.best(k)) for k in sorted(tuner.samples)}}

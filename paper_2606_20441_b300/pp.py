@@ -293,8 +293,10 @@ class Handle:
 
 
 def pp_propagate_batch(handles, instances, max_threads: int = 16, eps=None, w_max=None):
-    """pp_propagate for many handles at once (each handle on its own stream);
-    returns the per-item status list."""
+    """pp_propagate for many handles at once, in lockstep (handles of one
+    device, mask width and precision advance one fused sub-layer per step, each
+    kernel launched once per step for all of them); returns the per-item
+    status list.  max_threads is ignored by the library."""
     L = load_library()
     n = len(handles)
     keep = []
