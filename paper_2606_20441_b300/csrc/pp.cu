@@ -9,6 +9,7 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <string>
 #include <memory>
 #include <tuple>
@@ -772,15 +773,30 @@ struct KernelFacts {
     }
 };
 
+// Raises the kernel's dynamic shared-memory limit on the handle's device to at
+// least `smem`.  The limit only ever grows: handles that run concurrently with
+// different tile or table sizes must not lower it under each other's launches.
 template <typename K>
-cudaError_t prepare_kernel(const pp_handle* h, KernelFacts& f, K kernel, int threads, size_t smem, int* per_sm) {
+cudaError_t raise_smem_limit(const pp_handle* h, KernelFacts& f, K kernel, size_t smem) {
     const int dev = h->device;
     if (dev < 0 || dev >= KernelFacts::kDevices) return cudaErrorInvalidDevice;
     if (f.attr[dev].load() < smem) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        f.attr[dev].store(smem);
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lock(mu);
+        if (f.attr[dev].load() < smem) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            f.attr[dev].store(smem);
+        }
     }
+    return cudaSuccess;
+}
+
+template <typename K>
+cudaError_t prepare_kernel(const pp_handle* h, KernelFacts& f, K kernel, int threads, size_t smem, int* per_sm) {
+    const int dev = h->device;
+    cudaError_t e0 = raise_smem_limit(h, f, kernel, smem);
+    if (e0 != cudaSuccess) return e0;
     const unsigned long long o = f.occ[dev].load();
     int n = (int)(o >> 32);
     if (n == 0 || (o & 0xffffffffull) != (unsigned long long)smem) {
@@ -983,7 +999,10 @@ cudaError_t apply_noise(pp_handle* h, const NoiseHost& nh, int side, uint32_t B,
     const int grid = h->sm_count * 4;
     cudaError_t e;
 #define PP_NOISE_LAUNCH(WW, TT)                                                                         \
-    e = cudaFuncSetAttribute(k_noise<WW, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes); \
+    {                                                                                                   \
+        static KernelFacts facts;                                                                       \
+        e = raise_smem_limit(h, facts, k_noise<WW, TT>, L.bytes);                                       \
+    }                                                                                                   \
     if (e != cudaSuccess) return e;                                                                     \
     k_noise<WW, TT><<<grid, 256, L.bytes, h->st>>>(a.x, a.z, (TT*)a.c, h->cap, h->fill[side], B, C, o.x, o.z, \
                                                  (TT*)o.c, h->spill_cap, n_over, nz, n_pairs, eps, eps_f)
