@@ -332,6 +332,20 @@ def workload_serving(count: int = 2000, rate_hz: float = 200.0,
     return out
 
 
+def layer_range(inst: Instance, lo: int, hi: int) -> Instance:
+    """The instance restricted to its layers lo..hi-1 in time, renumbered from
+    0, with the noise maps attached to them; observable and truncation
+    unchanged.  Propagating through layers [k, L) and then, from the result,
+    through [0, k) is the same backward pass as through [0, L): a checkpoint
+    of a propagation is its exported result after the later layers."""
+    keep = (inst.layer_of >= lo) & (inst.layer_of < hi)
+    noise = [dataclasses.replace(m, layer=m.layer - lo) for m in inst.noise if lo <= m.layer < hi]
+    return dataclasses.replace(inst, name="%s[%d:%d]" % (inst.name, lo, hi), gate_x=inst.gate_x[keep],
+                               gate_z=inst.gate_z[keep], theta=inst.theta[keep],
+                               layer_of=(inst.layer_of[keep] - lo).astype(np.int32), n_layers=hi - lo,
+                               noise=noise)
+
+
 def mirror_instance(inst: Instance) -> Instance:
     """The circuit followed by its exact inverse (gates reversed, angles negated,
     no noise): the Heisenberg image of any observable is the observable itself

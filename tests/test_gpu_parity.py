@@ -398,17 +398,6 @@ def test_expectation_is_the_correctly_rounded_exact_sum(pp):
     assert got.expect == exact
 
 
-def _last_layers(inst, k):
-    """The instance restricted to its last k layers in time (the first k
-    layers of the backward pass)."""
-    import dataclasses
-    lo = inst.n_layers - k
-    keep = inst.layer_of >= lo
-    noise = [dataclasses.replace(m, layer=m.layer - lo) for m in inst.noise if m.layer >= lo]
-    return dataclasses.replace(inst, gate_x=inst.gate_x[keep], gate_z=inst.gate_z[keep], theta=inst.theta[keep],
-                               layer_of=(inst.layer_of[keep] - lo).astype(np.int32), n_layers=k, noise=noise)
-
-
 def test_sub_layer_rerun_keeps_its_input(pp):
     """Early sub-layers of this 7x8 instance grow its strings ~10x, far past
     the planner's estimate: the sixth sub-layer outgrows the capacity and runs
@@ -417,7 +406,7 @@ def test_sub_layer_rerun_keeps_its_input(pp):
     The result matches the oracle, twice in a row (runs are deterministic)."""
     import dataclasses
     inst = [i for i in inputs.workload_batch64(eps=1e-6) if i.name == "batch37"][0]
-    cut = dataclasses.replace(_last_layers(inst, 5), eps=1e-6, w_max=10)
+    cut = dataclasses.replace(inputs.layer_range(inst, inst.n_layers - 5, inst.n_layers), eps=1e-6, w_max=10)
     ref = oracle.run(cut)
     runs = [pp.propagate(cut) for _ in range(2)]
     for got in runs:
@@ -426,3 +415,22 @@ def test_sub_layer_rerun_keeps_its_input(pp):
         assert abs(got.expect - ref.expect) <= expect_tol((ref.x, ref.z, ref.c))
         assert got.stats.updates == ref.updates
     assert np.array_equal(runs[0].c, runs[1].c)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_checkpoint_and_resume(pp, precision):
+    """A propagation checkpointed after its later layers (the exported result)
+    and resumed through the earlier layers, in a fresh handle, gives the same
+    strings, coefficients and expectation as the uninterrupted propagation,
+    bit for bit, and the update counts add up."""
+    import dataclasses
+    inst = inputs.workload_6x6(steps=4, eps=1e-5)
+    k = inst.n_layers // 2
+    whole = pp.propagate(inst, precision=precision)
+    late = pp.propagate(inputs.layer_range(inst, k, inst.n_layers), precision=precision)
+    early = dataclasses.replace(inputs.layer_range(inst, 0, k), obs_x=late.x, obs_z=late.z, obs_c=late.c)
+    resumed = pp.propagate(early, precision=precision)
+    assert np.array_equal(resumed.x, whole.x) and np.array_equal(resumed.z, whole.z)
+    assert np.array_equal(resumed.c, whole.c)
+    assert resumed.expect == whole.expect
+    assert late.stats.updates + resumed.stats.updates == whole.stats.updates

@@ -404,3 +404,21 @@ def test_top_k_after_a_layer_closed_form():
     r = oracle.run(inst, top_k=k)
     assert {int(r.x[i, 0]) for i in range(len(r.c))} == want
     assert np.all(r.z[:, 0] == (1 << n) - 1)
+
+
+def test_checkpoint_split_is_the_same_pass():
+    """Propagating through the later layers, then from that result through the
+    earlier ones, is the same backward pass (Sec. I: the Heisenberg image is
+    taken gate by gate, truncation after every gate is idempotent on kept
+    strings): the same strings, coefficients, expectation and update count."""
+    import dataclasses
+    inst = inputs.workload_6x6(steps=2, eps=1e-5)
+    k = inst.n_layers // 2
+    whole = oracle.run(inst)
+    late = oracle.run(inputs.layer_range(inst, k, inst.n_layers))
+    early = dataclasses.replace(inputs.layer_range(inst, 0, k), obs_x=late.x, obs_z=late.z, obs_c=late.c)
+    resumed = oracle.run(early)
+    key = lambda r: {(tuple(x), tuple(z)): c for x, z, c in zip(r.x, r.z, r.c)}
+    assert key(resumed) == key(whole)
+    assert resumed.expect == whole.expect
+    assert late.updates + resumed.updates == whole.updates
