@@ -495,7 +495,8 @@ def pool_arm(args, rank, world, local_rank):
         [inputs.Request(i, 0.0, x) for i, x in enumerate(small)])
     ex.tuner = tuner
     torch.cuda.synchronize()
-    out = serving.Server(ex, n_workers=args.workers, n_large=n_large, route_key=autotune.class_key).serve(reqs)
+    out = serving.Server(ex, n_workers=args.workers, n_large=n_large, route_key=autotune.class_key,
+                         backlog="largest_first").serve(reqs)
     torch.cuda.synchronize()
     ex.close()
     torch.cuda.empty_cache()   # the workers' memory went back to torch's cache

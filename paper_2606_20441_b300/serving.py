@@ -139,13 +139,21 @@ def batch_order(requests: List["inputs.Request"]) -> List["inputs.Request"]:
 
 
 class Server:
-    """FIFO continuous batching: `n_workers` small-share workers and `n_large`
+    """Continuous batching: `n_workers` small-share workers and `n_large`
     large-share workers (indices after the small ones).  Large workers take
-    re-admitted requests first, then ordinary ones."""
+    re-admitted requests first, then ordinary ones.  `backlog` orders the
+    ordinary requests that are waiting when a worker frees up: "fifo" (arrival
+    order) or "largest_first" (the largest estimated cost first, ties by
+    arrival: under a backlog the longest propagations start first and the short
+    ones fill in around them, which shortens the span of a saturated stream;
+    with an empty backlog both take the next arrival)."""
 
     def __init__(self, executor, n_workers: int, n_large: int = 0,
                  clock: Callable[[], float] = time.perf_counter,
-                 route_key: Optional[Callable] = None):
+                 route_key: Optional[Callable] = None, backlog: str = "fifo"):
+        if backlog not in ("fifo", "largest_first"):
+            raise ValueError("backlog must be 'fifo' or 'largest_first'")
+        self.backlog = backlog
         self.executor = executor
         self.n_workers = n_workers
         self.n_large = n_large
@@ -162,7 +170,12 @@ class Server:
                         item = self._escalated.popleft()
                         break
                     if self._fresh:
-                        item = self._fresh.popleft()
+                        if self.backlog == "largest_first" and len(self._fresh) > 1:
+                            best = max(self._fresh, key=lambda it: (estimated_cost(it[0].instance), -it[1]))
+                            self._fresh.remove(best)
+                            item = best
+                        else:
+                            item = self._fresh.popleft()
                         break
                     if self._closed and self._pending == 0:
                         return

@@ -169,3 +169,22 @@ def test_cancel_running_and_queued_requests():
     assert out[reqs[2].rid].status == 0 and out[reqs[3].rid].status == 0
     assert time.perf_counter() - t0 < 2.0   # request 0 did not run its full service time
     assert not srv.cancel(reqs[2].rid)      # already finished
+
+
+def test_largest_first_backlog_order():
+    """With every request waiting at once and one worker, the largest-first
+    backlog runs them by decreasing estimated cost (qubits x layers); FIFO runs
+    them in arrival order."""
+    reqs = inputs.workload_serving(count=8, rate_hz=1e6, side_hi=6, steps_hi=8, eps_set=(1e-3,), w_max=6)
+    for backlog in ("fifo", "largest_first"):
+        ex = FakeExecutor()
+        out = serving.Server(ex, n_workers=1, backlog=backlog).serve(reqs, time_scale=0.0)
+        assert all(o.status == 0 for o in out)
+        by_name = {r.instance.name: r for r in reqs}
+        ran = [by_name[n] for n in ex.order]
+        if backlog == "fifo":
+            assert ran == sorted(reqs, key=lambda r: r.arrival_s)
+        else:
+            # the first request may start before the others are released
+            costs = [serving.estimated_cost(r.instance) for r in ran[1:]]
+            assert costs == sorted(costs, reverse=True)
