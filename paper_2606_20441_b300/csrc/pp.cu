@@ -707,20 +707,42 @@ pp_status ensure_memory(pp_handle* h, size_t want) {
 // bucket regions of `C` terms on arena `side`, their fill counters and
 // overflow offsets, and `n_over` grouped overflow terms.  Word w of a term
 // array starts at w * capacity, so each word's used prefix is copied to the
-// same index in the larger array; the layout's region size stays C.  On
+// same index in the larger array; the layout's region size stays C.  When
+// the device cannot hold `want` terms next to the old buffers, smaller
+// capacities down to `need` are tried (halving the step each time).  On
 // PP_ERR_NOMEM the handle keeps its old buffers and layout.
-pp_status grow_capacity(pp_handle* h, size_t want, int side, uint32_t B, uint64_t C, uint64_t n_over) {
-    const size_t cap = std::min(want, cap_limit(h));
+pp_status grow_capacity(pp_handle* h, size_t want, int side, uint32_t B, uint64_t C, uint64_t n_over,
+                        size_t need = 0) {
+    size_t cap = std::min(want, cap_limit(h));
     if (cap <= h->cap) return PP_OK;
+    // the new buffers are allocated while the old ones are still held: aim at
+    // what fits next to them (two arenas, two quarter-arena overflow areas and
+    // the per-bucket arrays: ~2.5 strings plus 4.5 bytes per term of
+    // capacity, and a margin), but not below `need`
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+        const double per = 2.5 * (double)term_bytes(h) + 4.5;
+        const double fit = std::max(0.0, (double)fr - (double)(1ull << 30)) / per;
+        if ((double)cap > fit) cap = std::max(need, (size_t)fit);
+        if (cap <= h->cap) return PP_OK;
+    } else {
+        cudaGetLastError();
+    }
     CapMem old = take_cap_memory(h);
-    pp_status st = alloc_cap_memory(h, cap);
-    if (st != PP_OK) {
+    pp_status st = PP_OK;
+    for (int attempt = 0;; ++attempt) {
+        st = alloc_cap_memory(h, cap);
+        if (st == PP_OK) break;
         std::string msg = h->err;
         CapMem part = take_cap_memory(h);
         free_cap_memory(h, part);
-        put_cap_memory(h, old);
-        h->err = msg;
-        return st;
+        const size_t smaller = std::max(need, old.cap + (cap - old.cap) / 2);
+        if (attempt >= 4 || need == 0 || smaller >= cap || smaller <= old.cap) {
+            put_cap_memory(h, old);
+            h->err = msg;
+            return st;
+        }
+        cap = smaller;
     }
     const size_t cb = h->opt.precision == PP_PRECISION_FP32 ? 4 : 8;
     const size_t n_reg = std::min<size_t>((size_t)B * C, old.cap);
@@ -1360,7 +1382,7 @@ pp_status prop_setup(Prop& P) {
         const double out = (double)P.N * P.growth_of(P.s);   // expected output
         // grow first when the output would fill more than half the buffers
         if (2.0 * out > (double)h->cap) {
-            pp_status st = grow_capacity(h, (size_t)(2.5 * out), P.side, P.B, P.C, P.n_over_in);
+            pp_status st = grow_capacity(h, (size_t)(2.5 * out), P.side, P.B, P.C, P.n_over_in, (size_t)(1.25 * out));
             if (st != PP_OK) return st;
         }
         const double est = std::max(64.0, out * 1.3);
@@ -1453,7 +1475,7 @@ pp_status prop_finish(Prop& P) {
     if ((ctr[CTR_ERR_REGION] || ctr[CTR_OUT] > h->cap) && P.attempt < 2) {
         P.growth[h->sub_kind[s]] = std::max(0.05, out / std::max<double>(1.0, (double)P.N));
         if (2.0 * out > (double)h->cap) {
-            pp_status st = grow_capacity(h, (size_t)(2.0 * out), P.side, P.B, P.C, P.n_over_in);
+            pp_status st = grow_capacity(h, (size_t)(2.0 * out), P.side, P.B, P.C, P.n_over_in, (size_t)(1.1 * out));
             if (st != PP_OK) return st;
         }
         if (out <= (double)h->cap) {
