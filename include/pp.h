@@ -109,8 +109,13 @@ pp_status pp_load_circuit(pp_handle* h, size_t n_gates, const uint64_t* rx, cons
  *   ex, ez   [n_gen][W] generators E_k;  lambda [n_gen] rates, >= 0
  *   mode     PP_NOISE_INVERSE: coefficients scale by exp(+2 sum lambda) (antinoise);
  *            PP_NOISE_FORWARD: by exp(-2 sum lambda) (the physical channel)
- * Generators of weight 1 and 2 are evaluated from per-site and per-pair tables;
- * heavier ones from a generic list.  Replaces a map previously attached to the layer. */
+ * The sum of the map's rates must be below 60 (below 40 on an FP32 handle, so
+ * that every factor stays within float range), else PP_ERR_ARG.
+ * Generators of weight 1 and 2 are evaluated from tables over groups of four
+ * sites plus per-pair corrections (exact fixed-point sums, units of 2^-56); heavier
+ * ones from a generic list.  The FP64 form multiplies by the factor in FP64; the
+ * FP32 form by the factor carried as a float pair, rounding the coefficient once.
+ * Replaces a map previously attached to the layer. */
 pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* ex,
                         const uint64_t* ez, const double* lambda, int mode);
 

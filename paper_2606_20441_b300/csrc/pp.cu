@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <string>
@@ -67,18 +68,22 @@ constexpr size_t kInitialCap = 1 << 16;  // first capacity of a handle without a
 struct NoiseHost {
     int mode = 0;
     std::vector<int64_t> t1;          // [n][4]  per-site sums incl. one-sided pair parts
+    int n = 0;                        // sites
+    std::vector<int64_t> grp;         // [(n+3)/4][256] group tables (NoiseDesc::grp)
     std::vector<int32_t> shift;       // [n_shift]
-    std::vector<uint64_t> smask;      // [n_shift][W]
+    std::vector<uint64_t> xmask;      // [n_shift][W] first sites of pairs that cross groups
     std::vector<int32_t> pidx;        // [n_shift][n]
     std::vector<int64_t> c2;          // [P][16]
     std::vector<uint64_t> gx, gz;
     std::vector<int64_t> glam;
     std::vector<double> etab;         // [8][256] exp(+-2 b 2^(8i-56))
+    std::vector<float> ftab;          // [8][256][2] the same as float (head, tail) pairs
     // device copies
     double* d_etab = nullptr;
-    int64_t* d_t1 = nullptr;
+    float* d_ftab = nullptr;
+    int64_t* d_grp = nullptr;
     int32_t* d_shift = nullptr;
-    uint64_t* d_smask = nullptr;
+    uint64_t* d_xmask = nullptr;
     int32_t* d_pidx = nullptr;
     int64_t* d_c2 = nullptr;
     uint64_t* d_gx = nullptr;
@@ -435,12 +440,13 @@ pp_status upload_tables(pp_handle* h) {
     add(h->subs.data(), sizeof(SubLayerDesc) * h->subs.size());
     for (auto& kv : h->noise) {
         NoiseHost& nh = kv.second;
-        add(nh.t1.data(), nh.t1.size() * 8);
+        add(nh.grp.data(), nh.grp.size() * 8);
         add(nh.shift.data(), nh.shift.size() * 4);
-        add(nh.smask.data(), nh.smask.size() * 8);
+        add(nh.xmask.data(), nh.xmask.size() * 8);
         add(nh.pidx.data(), nh.pidx.size() * 4);
         add(nh.c2.data(), nh.c2.size() * 8);
         add(nh.etab.data(), nh.etab.size() * 8);
+        add(nh.ftab.data(), nh.ftab.size() * 4);
         add(nh.gx.data(), nh.gx.size() * 8);
         add(nh.gz.data(), nh.gz.size() * 8);
         add(nh.glam.data(), nh.glam.size() * 8);
@@ -467,12 +473,13 @@ pp_status upload_tables(pp_handle* h) {
     h->d_subs = reinterpret_cast<SubLayerDesc*>(h->tab_dev + offs[k++]);
     for (auto& kv : h->noise) {
         NoiseHost& nh = kv.second;
-        nh.d_t1 = reinterpret_cast<int64_t*>(h->tab_dev + offs[k++]);
+        nh.d_grp = reinterpret_cast<int64_t*>(h->tab_dev + offs[k++]);
         nh.d_shift = reinterpret_cast<int32_t*>(h->tab_dev + offs[k++]);
-        nh.d_smask = reinterpret_cast<uint64_t*>(h->tab_dev + offs[k++]);
+        nh.d_xmask = reinterpret_cast<uint64_t*>(h->tab_dev + offs[k++]);
         nh.d_pidx = reinterpret_cast<int32_t*>(h->tab_dev + offs[k++]);
         nh.d_c2 = reinterpret_cast<int64_t*>(h->tab_dev + offs[k++]);
         nh.d_etab = reinterpret_cast<double*>(h->tab_dev + offs[k++]);
+        nh.d_ftab = reinterpret_cast<float*>(h->tab_dev + offs[k++]);
         nh.d_gx = reinterpret_cast<uint64_t*>(h->tab_dev + offs[k++]);
         nh.d_gz = reinterpret_cast<uint64_t*>(h->tab_dev + offs[k++]);
         nh.d_glam = reinterpret_cast<int64_t*>(h->tab_dev + offs[k++]);
@@ -994,14 +1001,16 @@ NoiseDesc noise_desc(const NoiseHost& nh) {
     NoiseDesc d;
     d.mode = nh.mode;
     d.n_generic = (int)nh.glam.size();
-    d.t1 = nh.d_t1;
     d.n_shift = (int)nh.shift.size();
-    d.n_sites = (int)(nh.t1.size() / 4);
+    d.n_sites = nh.n;
+    d.n_groups = (nh.n + 3) / 4;
+    d.grp = nh.d_grp;
     d.shift = nh.d_shift;
-    d.smask = nh.d_smask;
+    d.xmask = nh.d_xmask;
     d.pidx = nh.d_pidx;
     d.c2 = nh.d_c2;
     d.etab = nh.d_etab;
+    d.ftab = nh.d_ftab;
     d.gen_x = nh.d_gx;
     d.gen_z = nh.d_gz;
     d.gen_lam = nh.d_glam;
@@ -1014,19 +1023,19 @@ cudaError_t apply_noise(pp_handle* h, const NoiseHost& nh, int side, uint32_t B,
                         double eps, float eps_f, int* launches) {
     NoiseDesc nz = noise_desc(nh);
     const int n_pairs = (int)(nh.c2.size() / 16);
-    const NoiseSmem L = noise_smem_layout(nz.n_sites, nz.n_shift, n_pairs, h->W);
+    const NoiseSmem L = noise_smem_layout(nz.n_sites, nz.n_groups, nz.n_shift, n_pairs, h->W);
     const bool f32 = h->opt.precision == PP_PRECISION_FP32;
     const Arena& a = h->arena[side];
     const Arena& o = h->spill_grp;
-    const int grid = h->sm_count * 4;
+    int per_sm = 1;
     cudaError_t e;
 #define PP_NOISE_LAUNCH(WW, TT)                                                                         \
     {                                                                                                   \
         static KernelFacts facts;                                                                       \
-        e = raise_smem_limit(h, facts, k_noise<WW, TT>, L.bytes);                                       \
+        e = prepare_kernel(h, facts, k_noise<WW, TT>, 256, L.bytes, &per_sm);                           \
     }                                                                                                   \
     if (e != cudaSuccess) return e;                                                                     \
-    k_noise<WW, TT><<<grid, 256, L.bytes, h->st>>>(a.x, a.z, (TT*)a.c, h->cap, h->fill[side], B, C, o.x, o.z, \
+    k_noise<WW, TT><<<h->sm_count * std::min(per_sm, 8), 256, L.bytes, h->st>>>(a.x, a.z, (TT*)a.c, h->cap, h->fill[side], B, C, o.x, o.z, \
                                                  (TT*)o.c, h->spill_cap, n_over, nz, n_pairs, eps, eps_f)
     if (h->W == 1) {
         if (f32) { PP_NOISE_LAUNCH(1, float); } else { PP_NOISE_LAUNCH(1, double); }
@@ -1912,7 +1921,8 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
     const int W = h->W, n = h->n;
     NoiseHost nh;
     nh.mode = mode;
-    nh.t1.assign((size_t)n * 4, 0);
+    nh.n = n;
+    std::vector<int64_t> t1((size_t)n * 4, 0);   // [n][4] per-site sums, by letter on the site
     std::map<std::pair<int, int>, int> pid;
     std::vector<std::pair<int, int>> pairs;
     std::vector<int64_t> t2;            // [P][16] sum over 2-local generators on the pair
@@ -1938,7 +1948,7 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
             int q = sites[0];
             int e = bit(x, q) + 2 * bit(z, q);
             for (int l = 1; l < 4; ++l)
-                if (anti1(l, e)) nh.t1[4 * q + l] += lf;
+                if (anti1(l, e)) t1[4 * q + l] += lf;
         } else if (sites.size() == 2) {
             int a = sites[0], b = sites[1];
             auto key = std::make_pair(a, b);
@@ -1963,22 +1973,48 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
         }
     }
     if (total >= 60.0) return fail(h, PP_ERR_ARG, "sum of rates %.3g too large (must be < 60)", total);
+    if (h->opt.precision == PP_PRECISION_FP32 && total >= 40.0)
+        return fail(h, PP_ERR_ARG, "sum of rates %.3g too large for the FP32 form (must be < 40)", total);
     // Fold each pair's one-sided terms (the other site carries I) into the
     // per-site table; keep, per pair, the correction for strings that hold a
     // non-identity letter on both sites:
     //   T2[la,lb] = T2[la,I] + T2[I,lb] + C[la,lb]   (exact integers).
-    nh.c2.assign(16 * pairs.size(), 0);
-    std::map<int, int> shift_class;
+    std::vector<int64_t> corr(16 * pairs.size(), 0);
     for (size_t i = 0; i < pairs.size(); ++i) {
         const int a = pairs[i].first, b = pairs[i].second;
         const int64_t* T = &t2[16 * i];
         for (int l = 1; l < 4; ++l) {
-            nh.t1[4 * a + l] += T[l];          // (l, I)
-            nh.t1[4 * b + l] += T[4 * l];      // (I, l)
+            t1[4 * a + l] += T[l];          // (l, I)
+            t1[4 * b + l] += T[4 * l];      // (I, l)
         }
         for (int la = 1; la < 4; ++la)
             for (int lb = 1; lb < 4; ++lb)
-                nh.c2[16 * i + la + 4 * lb] = T[la + 4 * lb] - T[la] - T[4 * lb];
+                corr[16 * i + la + 4 * lb] = T[la + 4 * lb] - T[la] - T[4 * lb];
+    }
+    // Group tables over sites 4g..4g+3, indexed by the group's x nibble | z
+    // nibble << 4: the per-site terms of the four letters, plus the correction
+    // of every pair inside the group.  The exponent is a sum of exact integers,
+    // so this regrouping leaves it unchanged.
+    const int ng = (n + 3) / 4;
+    auto letter = [](int idx, int j) { return ((idx >> j) & 1) + 2 * ((idx >> (4 + j)) & 1); };
+    nh.grp.assign((size_t)ng * 256, 0);
+    for (int g = 0; g < ng; ++g)
+        for (int idx = 0; idx < 256; ++idx) {
+            int64_t v = 0;
+            for (int j = 0; j < 4 && 4 * g + j < n; ++j) v += t1[4 * (4 * g + j) + letter(idx, j)];
+            nh.grp[256 * (size_t)g + idx] = v;
+        }
+    // Pairs across groups keep their correction, reached through the shift
+    // class of the pair and its first site.
+    std::map<int, int> shift_class;
+    for (size_t i = 0; i < pairs.size(); ++i) {
+        const int a = pairs[i].first, b = pairs[i].second;
+        if ((a >> 2) == (b >> 2)) {
+            const int g = a >> 2;
+            for (int idx = 0; idx < 256; ++idx)
+                nh.grp[256 * (size_t)g + idx] += corr[16 * i + letter(idx, a & 3) + 4 * letter(idx, b & 3)];
+            continue;
+        }
         const int d = b - a;
         auto it = shift_class.find(d);
         int c;
@@ -1986,22 +2022,35 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
             c = (int)nh.shift.size();
             shift_class[d] = c;
             nh.shift.push_back(d);
-            nh.smask.resize(nh.smask.size() + W, 0);
+            nh.xmask.resize(nh.xmask.size() + W, 0);
             nh.pidx.resize(nh.pidx.size() + n, -1);
         } else {
             c = it->second;
         }
-        nh.smask[(size_t)c * W + (a >> 6)] |= 1ull << (a & 63);
-        nh.pidx[(size_t)c * n + a] = (int32_t)i;
+        nh.xmask[(size_t)c * W + (a >> 6)] |= 1ull << (a & 63);
+        nh.pidx[(size_t)c * n + a] = (int32_t)(nh.c2.size() / 16);
+        nh.c2.insert(nh.c2.end(), corr.begin() + 16 * i, corr.begin() + 16 * (i + 1));
     }
     h->noise.erase(layer);
     // factor tables: entry (i, b) = exp(+-2 * b * 2^(8i - 56)), evaluated in extended
-    // precision and rounded once to double
+    // precision and rounded once to double, and as a float (head, tail) pair: the
+    // head rounded to float, the tail the rounded remainder.  Entries beyond the
+    // float range (byte 7 above 44, unreachable under the rate limit of the FP32
+    // form) saturate.
     nh.etab.assign(8 * 256, 1.0);
+    nh.ftab.assign(8 * 256 * 2, 0.0f);
     for (int i = 0; i < 8; ++i)
-        for (int b = 1; b < 256; ++b) {
-            long double e = std::ldexp((long double)b, 8 * i - FIX_SHIFT) * 2.0L;
-            nh.etab[256 * i + b] = (double)std::exp(mode == PP_NOISE_INVERSE ? e : -e);
+        for (int b = 0; b < 256; ++b) {
+            const long double e = std::ldexp((long double)b, 8 * i - FIX_SHIFT) * 2.0L;
+            const long double v = std::exp(mode == PP_NOISE_INVERSE ? e : -e);
+            nh.etab[256 * i + b] = (double)v;
+            float hd = std::numeric_limits<float>::max(), tl = 0.0f;
+            if (v < (long double)std::numeric_limits<float>::max()) {
+                hd = (float)v;
+                tl = (float)(v - (long double)hd);
+            }
+            nh.ftab[2 * (256 * i + b)] = hd;
+            nh.ftab[2 * (256 * i + b) + 1] = tl;
         }
     h->noise[layer] = std::move(nh);
     h->have_result = false;

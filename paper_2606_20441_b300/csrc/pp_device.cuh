@@ -91,17 +91,21 @@ struct ActDesc {
 
 // Sparse Pauli-Lindblad map evaluated from tables.  Letter code l = x + 2z
 // (I=0, X=1, Z=2, Y=3).  Exponents are 64-bit fixed point (2^-56 units), summed
-// exactly.
+// exactly, so any grouping of the terms gives the same exponent.
 struct NoiseDesc {
     int mode;                     // 0: exp(+2s), 1: exp(-2s)
     int n_generic;
     int n_shift;                  // classes of 2-local generator supports (a, a + shift)
     int n_sites;
-    const int64_t* t1;            // [n][4]  sum of lambda over every 1- or 2-local generator
-                                  //         touching q that anticommutes with letter l on q
-                                  //         (identity on the rest of its support)
+    int n_groups;                 // 4-site groups, (n_sites + 3) / 4
+    const int64_t* grp;           // [n_groups][256] exponent part of group g (sites 4g..4g+3) by
+                                  //   its letters, index (x nibble) | (z nibble) << 4: for each
+                                  //   site, every 1- or 2-local generator touching it that
+                                  //   anticommutes with its letter there (identity on the rest
+                                  //   of its support), plus the correction of each pair inside
+                                  //   the group
     const int32_t* shift;         // [n_shift] site distance of the class
-    const uint64_t* smask;        // [n_shift][W] first sites of the class's pairs
+    const uint64_t* xmask;        // [n_shift][W] first sites of the class's pairs that cross groups
     const int32_t* pidx;          // [n_shift][n] pair starting at site a in the class, or -1
     const int64_t* c2;            // [P][16] correction for pairs with both sites in the
                                   //         support: T2[la,lb] - T2[la,I] - T2[I,lb], index la + 4 lb
@@ -109,7 +113,9 @@ struct NoiseDesc {
     const uint64_t* gen_z;
     const int64_t* gen_lam;
     const double* etab;           // [8][256] exp(+-2 * b * 2^(8i - 56)): factor tables by
-                                  //          byte i of the fixed-point exponent
+                                  //          byte i of the fixed-point exponent (FP64 form)
+    const float* ftab;            // [8][256][2] the same factors as float pairs (head, tail),
+                                  //          head + tail within 2^-48 of the factor (FP32 form)
 };
 
 // ----------------------------------------------------------------------------- bit helpers
@@ -382,39 +388,48 @@ __device__ __forceinline__ uint32_t bucket_of(const D& d, const uint64_t* x, con
 
 // ----------------------------------------------------------------------------- noise
 
-// Exponent sum_{k: {P,E_k} = 0} lambda_k in 2^-56 fixed point: per-site terms
-// over supp(P) (which already hold the one-sided part of every pair), plus a
-// correction for each generator pair whose two sites are both in supp(P).
+// Exponent sum_{k: {P,E_k} = 0} lambda_k in 2^-56 fixed point: one table entry
+// per 4-site group (the per-site terms, which already hold the one-sided part of
+// every pair, and the pairs inside the group), plus a correction for each pair
+// that crosses groups with both sites in supp(P), plus the heavier generators.
 template <int W>
 __device__ __forceinline__ int64_t noise_exponent(const NoiseDesc& nz, const uint64_t* x,
                                                   const uint64_t* z) {
     int64_t s = 0;
-    uint64_t sup[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        sup[w] = x[w] | z[w];
-        uint64_t m = sup[w];
-        while (m) {
-            const int b = __ffsll((long long)m) - 1;
-            m &= m - 1;
-            const int lq = (int)((x[w] >> b) & 1ull) + 2 * (int)((z[w] >> b) & 1ull);
-            s += nz.t1[4 * (64 * w + b) + lq];
+        const uint32_t xl = (uint32_t)x[w], xh = (uint32_t)(x[w] >> 32);
+        const uint32_t zl = (uint32_t)z[w], zh = (uint32_t)(z[w] >> 32);
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const int G = 16 * w + g;
+            if (G < nz.n_groups) {
+                const uint32_t xv = g < 8 ? xl : xh, zv = g < 8 ? zl : zh;
+                const int sh = 4 * (g & 7);
+                const uint32_t idx = ((xv >> sh) & 15u) | (((zv >> sh) << 4) & 0xf0u);
+                s += nz.grp[256 * G + idx];
+            }
         }
     }
-    for (int c = 0; c < nz.n_shift; ++c) {
-        const int d = nz.shift[c];
-        uint64_t sh[W];
-        shr_words<W>(sup, d, sh);
+    if (nz.n_shift) {
+        uint64_t sup[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            uint64_t both = sup[w] & sh[w] & nz.smask[(size_t)c * W + w];
-            while (both) {
-                const int bpos = __ffsll((long long)both) - 1;
-                both &= both - 1;
-                const int a = 64 * w + bpos, bq = a + d;
-                const int la = (int)((x[w] >> bpos) & 1ull) + 2 * (int)((z[w] >> bpos) & 1ull);
-                const int lb = (int)((x[bq >> 6] >> (bq & 63)) & 1ull) + 2 * (int)((z[bq >> 6] >> (bq & 63)) & 1ull);
-                s += nz.c2[16 * nz.pidx[(size_t)c * nz.n_sites + a] + la + 4 * lb];
+        for (int w = 0; w < W; ++w) sup[w] = x[w] | z[w];
+        for (int c = 0; c < nz.n_shift; ++c) {
+            const int d = nz.shift[c];
+            uint64_t sh[W];
+            shr_words<W>(sup, d, sh);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint64_t both = sup[w] & sh[w] & nz.xmask[(size_t)c * W + w];
+                while (both) {
+                    const int bpos = __ffsll((long long)both) - 1;
+                    both &= both - 1;
+                    const int a = 64 * w + bpos, bq = a + d;
+                    const int la = (int)((x[w] >> bpos) & 1ull) + 2 * (int)((z[w] >> bpos) & 1ull);
+                    const int lb = (int)((x[bq >> 6] >> (bq & 63)) & 1ull) + 2 * (int)((z[bq >> 6] >> (bq & 63)) & 1ull);
+                    s += nz.c2[16 * nz.pidx[(size_t)c * nz.n_sites + a] + la + 4 * lb];
+                }
             }
         }
     }
@@ -427,8 +442,7 @@ __device__ __forceinline__ int64_t noise_exponent(const NoiseDesc& nz, const uin
 // exp(+-2 s) for s = S * 2^-56 (S >= 0), as the product over the bytes of S of
 // host-tabulated factors: exp(a + b) = exp(a) exp(b), so at most seven FP64
 // multiplies instead of an FP64 exponential.  Each table entry is the exponential
-// correctly rounded to double; the product carries at most a few ulp.  Both
-// coefficient precisions use it: the FP32 form rounds c * f once (Coef::scale).
+// correctly rounded to double; the product carries at most a few ulp.
 __device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t S) {
     uint64_t u = (uint64_t)S;
     double f = 1.0;
@@ -440,14 +454,36 @@ __device__ __forceinline__ double noise_factor(const NoiseDesc& nz, int64_t S) {
     return f;
 }
 
+// The same product carried as an unevaluated float pair (head h, tail l), on the
+// FP32 pipe (the FP64 pipe is narrow on this part).  Each step multiplies the
+// pair by a table pair: the exact product of the heads (an FMA recovers its
+// rounding error), the two cross terms folded into that error, and a Fast2Sum
+// that renormalises; the tail-by-tail term (below 2^-48 relative) is dropped.
+// Entry 0 of every byte table is (1, 0), so every byte takes the same path.  The
+// pair stays within ~2^-44 of the factor (the product of eight steps).
+__device__ __forceinline__ void noise_factor_pair(const NoiseDesc& nz, int64_t S, float& h, float& l) {
+    const uint64_t u = (uint64_t)S;
+    h = 1.0f;
+    l = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t byte = (uint32_t)(u >> (8 * i)) & 0xffu;
+        const float2 t = reinterpret_cast<const float2*>(nz.ftab)[256 * i + byte];
+        const float p = __fmul_rn(h, t.x);
+        float e = __fmaf_rn(h, t.x, -p);
+        e = __fmaf_rn(h, t.y, e);
+        e = __fmaf_rn(l, t.x, e);
+        h = __fadd_rn(p, e);
+        l = __fsub_rn(e, __fsub_rn(h, p));
+    }
+}
+
 // ----------------------------------------------------------------------------- coefficient ops
 
 template <typename T> struct Coef;
 
 template <> struct Coef<double> {
     __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    // c times a noise factor
-    __device__ static __forceinline__ double scale(double c, double f) { return __dmul_rn(c, f); }
     __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     // cs*c + phi*(sn*c2): exactly the oracle's two contributions, no fused multiply-add
     __device__ static __forceinline__ double rot(double cs, double c, double sn, double c2, int phi) {
@@ -464,10 +500,6 @@ template <> struct Coef<double> {
 
 template <> struct Coef<float> {
     __device__ static __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-    // c times a noise factor, in FP64, rounded once to float
-    __device__ static __forceinline__ float scale(float c, double f) {
-        return __double2float_rn(__dmul_rn((double)c, f));
-    }
     __device__ static __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     // Compensated cs*c + phi*sn*c2: error-free products (FMA residuals) and an
     // error-free sum, folded into one final rounding (Ogita-Rump-Oishi Dot2).
@@ -488,6 +520,20 @@ template <> struct Coef<float> {
         return m == 0 || m < e;
     }
 };
+
+// c times the noise factor of exponent S.  FP64 form: the FP64 factor, one
+// rounding.  FP32 form: c * (h + l) as one FMA over the float pair, c * l rounded
+// first (its error is below 2^-48 of the result), so the coefficient is rounded
+// once, to within ~2^-44 of c times the exact factor.
+template <typename T> __device__ T noise_scale(const NoiseDesc& nz, T c, int64_t S);
+template <> __device__ __forceinline__ double noise_scale<double>(const NoiseDesc& nz, double c, int64_t S) {
+    return __dmul_rn(c, noise_factor(nz, S));
+}
+template <> __device__ __forceinline__ float noise_scale<float>(const NoiseDesc& nz, float c, int64_t S) {
+    float h, l;
+    noise_factor_pair(nz, S, h, l);
+    return __fmaf_rn(c, h, __fmul_rn(c, l));
+}
 
 // The exact expectation sum: every diagonal coefficient becomes trunc(v * 2^80)
 // as a 128-bit integer and the integers are added.  Coefficients must be finite

@@ -526,7 +526,7 @@ __device__ bool process_bucket(const Tile<W, T, I>& t, const GateTab<W, T>& tab,
                 if (Coef<T>::small(c, eps) || (p.w_max >= 0 && weight_of<W>(x, z) > p.w_max)) c = T(0);
             }
             if (p.has_noise && c != T(0)) {
-                c = Coef<T>::scale(c, noise_factor(p.noise, noise_exponent<W>(p.noise, x, z)));
+                c = noise_scale<T>(p.noise, c, noise_exponent<W>(p.noise, x, z));
                 if (Coef<T>::small(c, eps)) c = T(0);
             }
             t.c[i] = c;
@@ -1138,17 +1138,21 @@ __global__ void k_spill_move(const uint64_t* rx, const uint64_t* rz, const T* rc
 
 // Shared-memory copy of a noise map's tables (sizes fixed per map).
 struct NoiseSmem {
-    size_t t1, shift, smask, pidx, c2, etab;   // byte offsets
+    size_t grp, shift, xmask, pidx, c2, ftab;   // byte offsets
     size_t bytes;
 };
 
-__host__ __device__ inline NoiseSmem noise_smem_layout(int n_sites, int n_shift, int n_pairs, int W) {
+// Shared-memory copy of a map's tables: the factor table of the coefficient
+// type (FP64 entries, or float pairs: 16 KB either way), the group tables, the
+// pair corrections and the cross-group pair index.
+__host__ __device__ inline NoiseSmem noise_smem_layout(int n_sites, int n_groups, int n_shift, int n_pairs,
+                                                       int W) {
     NoiseSmem L;
     size_t o = 0;
-    L.etab = o; o += sizeof(double) * 8 * 256;
-    L.t1 = o; o += sizeof(int64_t) * 4 * (size_t)n_sites;
+    L.ftab = o; o += sizeof(double) * 8 * 256;
+    L.grp = o; o += sizeof(int64_t) * 256 * (size_t)n_groups;
     L.c2 = o; o += sizeof(int64_t) * 16 * (size_t)n_pairs;
-    L.smask = o; o += sizeof(uint64_t) * (size_t)n_shift * W;
+    L.xmask = o; o += sizeof(uint64_t) * (size_t)n_shift * W;
     L.shift = o; o += sizeof(int32_t) * (size_t)n_shift;
     L.pidx = o; o += sizeof(int32_t) * (size_t)n_shift * n_sites;
     L.bytes = (o + 15) & ~(size_t)15;
@@ -1165,26 +1169,28 @@ __global__ void __launch_bounds__(256) k_noise(const uint64_t* x, const uint64_t
                                                uint64_t n_over, NoiseDesc nz, int n_pairs, double eps,
                                                float eps_f) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const NoiseSmem L = noise_smem_layout(nz.n_sites, nz.n_shift, n_pairs, W);
+    const NoiseSmem L = noise_smem_layout(nz.n_sites, nz.n_groups, nz.n_shift, n_pairs, W);
     {
         auto cp = [&](size_t off, const void* src, size_t bytes) {
             const uint32_t* s32 = static_cast<const uint32_t*>(src);
             uint32_t* d32 = reinterpret_cast<uint32_t*>(smem + off);
             for (size_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d32[i] = s32[i];
         };
-        cp(L.etab, nz.etab, sizeof(double) * 8 * 256);
-        cp(L.t1, nz.t1, sizeof(int64_t) * 4 * (size_t)nz.n_sites);
+        cp(L.ftab, sizeof(T) == 8 ? static_cast<const void*>(nz.etab) : static_cast<const void*>(nz.ftab),
+           sizeof(double) * 8 * 256);
+        cp(L.grp, nz.grp, sizeof(int64_t) * 256 * (size_t)nz.n_groups);
         cp(L.c2, nz.c2, sizeof(int64_t) * 16 * (size_t)n_pairs);
-        cp(L.smask, nz.smask, sizeof(uint64_t) * (size_t)nz.n_shift * W);
+        cp(L.xmask, nz.xmask, sizeof(uint64_t) * (size_t)nz.n_shift * W);
         cp(L.shift, nz.shift, sizeof(int32_t) * (size_t)nz.n_shift);
         cp(L.pidx, nz.pidx, sizeof(int32_t) * (size_t)nz.n_shift * nz.n_sites);
     }
     __syncthreads();
     NoiseDesc sn = nz;
-    sn.etab = reinterpret_cast<const double*>(smem + L.etab);
-    sn.t1 = reinterpret_cast<const int64_t*>(smem + L.t1);
+    sn.etab = reinterpret_cast<const double*>(smem + L.ftab);
+    sn.ftab = reinterpret_cast<const float*>(smem + L.ftab);
+    sn.grp = reinterpret_cast<const int64_t*>(smem + L.grp);
     sn.c2 = reinterpret_cast<const int64_t*>(smem + L.c2);
-    sn.smask = reinterpret_cast<const uint64_t*>(smem + L.smask);
+    sn.xmask = reinterpret_cast<const uint64_t*>(smem + L.xmask);
     sn.shift = reinterpret_cast<const int32_t*>(smem + L.shift);
     sn.pidx = reinterpret_cast<const int32_t*>(smem + L.pidx);
     const T e = sizeof(T) == 8 ? T(eps) : T(eps_f);
@@ -1198,7 +1204,7 @@ __global__ void __launch_bounds__(256) k_noise(const uint64_t* x, const uint64_t
             xx[w] = ax[(size_t)w * acap + i];
             zz[w] = az[(size_t)w * acap + i];
         }
-        v = Coef<T>::scale(v, noise_factor(sn, noise_exponent<W>(sn, xx, zz)));
+        v = noise_scale<T>(sn, v, noise_exponent<W>(sn, xx, zz));
         if (Coef<T>::small(v, e)) v = T(0);
         ac[i] = v;
     };

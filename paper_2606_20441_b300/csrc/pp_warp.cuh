@@ -104,7 +104,7 @@ __device__ bool warp_bucket(const Tile<W, T, int16_t>& t, const GateTab<W, T>& t
                 if (Coef<T>::small(c, eps) || (p.w_max >= 0 && weight_of<W>(x, z) > p.w_max)) c = T(0);
             }
             if (p.has_noise && c != T(0)) {
-                c = Coef<T>::scale(c, noise_factor(p.noise, noise_exponent<W>(p.noise, x, z)));
+                c = noise_scale<T>(p.noise, c, noise_exponent<W>(p.noise, x, z));
                 if (Coef<T>::small(c, eps)) c = T(0);
             }
             t.c[i] = c;

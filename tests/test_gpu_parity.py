@@ -338,6 +338,31 @@ def test_bench_configuration_theta_zero(pp):
     assert got.stats.updates == inst.n_gates * len(inst.obs_c)
 
 
+def test_bench_configuration_theta_zero_fp32_rounds_once_per_map(pp):
+    """The FP32 form of the zero-angle benchmark configuration: each noise map
+    multiplies a coefficient by its exact factor exp(2 S 2^-56) (S the map's
+    fixed-point exponent, an integer sum) and rounds once to float.  The factor
+    is carried as a float pair; a pair that lost its tail (a plain float
+    product) would be off by several ulp per map, twenty maps in a row."""
+    from fractions import Fraction
+    inst = _bench_shaped(0.0, 0.0)
+    got = pp.propagate(inst, precision=32)
+    assert len(got.c) == len(inst.obs_c)
+    fix = [[int(Fraction(float(v)) * 2 ** 56 + Fraction(1, 2)) for v in m.lam] for m in inst.noise]
+    exact = 0
+    for t in range(len(inst.obs_c)):
+        c = np.float32(inst.obs_c[t])
+        for m, lf in sorted(zip(inst.noise, fix), key=lambda ml: -ml[0].layer):
+            anti = np.bitwise_and(m.ex[:, 0], inst.obs_z[t, 0]) ^ np.bitwise_and(m.ez[:, 0], inst.obs_x[t, 0])
+            S = sum(v for v, a in zip(lf, anti) if bin(int(a)).count("1") & 1)
+            c = np.float32(float(c) * math.exp(2.0 * math.ldexp(S, -56)))
+        i = int(np.nonzero((got.x[:, 0] == inst.obs_x[t, 0]) & (got.z[:, 0] == inst.obs_z[t, 0]))[0][0])
+        g = np.float32(got.c[i])
+        assert abs(float(g) - float(c)) <= 2 * float(np.spacing(c)), (t, g, c)
+        exact += int(g == c)
+    assert exact >= 0.95 * len(inst.obs_c)
+
+
 # ----------------------------------------------------------------- top-K truncation
 
 TOPK_CASES = {"6x6_s3": lambda: inputs.workload_6x6(steps=3, eps=1e-5),
