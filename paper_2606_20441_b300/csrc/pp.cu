@@ -67,7 +67,6 @@ constexpr size_t kInitialCap = 1 << 16;  // first capacity of a handle without a
 
 struct NoiseHost {
     int mode = 0;
-    std::vector<int64_t> t1;          // [n][4]  per-site sums incl. one-sided pair parts
     int n = 0;                        // sites
     std::vector<int64_t> grp;         // [(n+3)/4][256] group tables (NoiseDesc::grp)
     std::vector<int32_t> shift;       // [n_shift]
