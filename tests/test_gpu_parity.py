@@ -201,6 +201,36 @@ def test_observable_coefficients_must_be_finite_and_below_2_32(pp):
     h.close()
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("layer", [1, 0])
+def test_noise_rate_limits_and_largest_factors(pp, precision, layer):
+    """A map's rates must sum below 60 (below 40 in the FP32 form, whose
+    factors must stay within float range); factors up to the limit are exact
+    to the form's precision.  One qubit, two layers of one identity gate each,
+    the map {X: a, Z: a} after layer 1 (the first sub-layer's prologue applies
+    it) or after layer 0 (the streaming pass): X and Z anticommute with one
+    generator each (factor e^{2a}), Y with both (e^{4a}); byte 7 of the
+    fixed-point exponent carries the integer part."""
+    zx = np.zeros((2, 1), np.uint64)
+    one = np.ones((2, 1), np.uint64)
+    h = pp.Handle(1, precision=precision)
+    h.pp_load_circuit(one, zx, np.array([0.0, 0.0]), np.array([0, 1], np.int32), 2)
+    gx, gz = np.array([[1], [0]], np.uint64), np.array([[0], [1]], np.uint64)
+    limit = 60.0 if precision == 64 else 40.0
+    with pytest.raises(pp.PPError):
+        h.pp_load_noise(layer, gx, gz, np.array([limit / 2, limit / 2 + 0.5]))
+    a = limit / 2 - 0.5
+    h.pp_load_noise(layer, gx, gz, np.array([a, a]))
+    tol = 1e-13 if precision == 64 else 2.0 ** -22
+    for (ox, oz), k in (((1, 0), 1), ((0, 1), 1), ((1, 1), 2)):
+        h.pp_propagate(np.array([[ox]], np.uint64), np.array([[oz]], np.uint64), np.array([1.0]), 0.0, -1)
+        x, z, c = h.pp_export_terms()
+        want = math.exp(2.0 * k * a)
+        assert len(c) == 1 and int(x[0, 0]) == ox and int(z[0, 0]) == oz
+        assert abs(c[0] - want) <= tol * want, (ox, oz, c[0], want)
+    h.close()
+
+
 # ----------------------------------------------------------------- every processing tier
 
 TIER_CASES = {"6x6_s3": lambda: inputs.workload_6x6(steps=3, eps=1e-5),
