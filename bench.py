@@ -496,7 +496,7 @@ def pool_arm(args, rank, world, local_rank):
     ex.tuner = tuner
     torch.cuda.synchronize()
     out = serving.Server(ex, n_workers=args.workers, n_large=n_large, route_key=autotune.class_key,
-                         backlog="largest_first").serve(reqs)
+                         backlog="largest_first", exclusive=True).serve(reqs)
     torch.cuda.synchronize()
     ex.close()
     torch.cuda.empty_cache()   # the workers' memory went back to torch's cache

@@ -92,6 +92,32 @@ NOALLOC_MAX_TERMS = 1 << 27
 _lib = None
 
 
+def _guarded_alloc(fn):
+    """An allocation callback for the library: fn(nbytes) returns a device
+    pointer.  Whatever fn raises (torch's OutOfMemoryError, say) becomes NULL,
+    which the library reports as PP_ERR_NOMEM with the handle intact.  The
+    guard is required: an exception escaping a ctypes callback leaves its
+    return value unset, and the library would receive an arbitrary pointer."""
+    def cb(nbytes, ctx):
+        try:
+            ptr = fn(int(nbytes))
+            return int(ptr) if ptr else None
+        except BaseException:   # nothing may propagate into C; NULL reports the failure
+            return None
+    return cb
+
+
+def _guarded_free(fn):
+    """A free callback for the library; an exception from fn(ptr) is dropped
+    (it cannot propagate into C)."""
+    def cb(ptr, ctx):
+        try:
+            fn(ptr)
+        except BaseException:   # nothing may propagate into C
+            pass
+    return cb
+
+
 def load_library(path: Optional[str] = None):
     """Loads libpp.so (raises OSError if it was not built).  The environment
     variable PP_LIBRARY selects another build of the library, e.g. the debug
@@ -155,8 +181,7 @@ class Handle:
         self._cb = None
         if allocator is not None:
             a_fn, f_fn = allocator
-            self._cb = (ALLOC_FN(lambda nbytes, ctx: a_fn(int(nbytes)) or None),
-                        FREE_FN(lambda ptr, ctx: f_fn(ptr)))
+            self._cb = (ALLOC_FN(_guarded_alloc(a_fn)), FREE_FN(_guarded_free(f_fn)))
             opt.alloc, opt.free = self._cb
             if stream is not None:
                 opt.cuda_stream = stream
@@ -166,13 +191,8 @@ class Handle:
             # blocks are cached per stream: allocate on the stream that uses them
             st = torch.cuda.current_stream().cuda_stream if stream is None else stream
 
-            def _alloc(nbytes, ctx):
-                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
-
-            def _free(ptr, ctx):
-                torch.cuda.caching_allocator_delete(ptr)
-
-            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            self._cb = (ALLOC_FN(_guarded_alloc(lambda n: torch.cuda.caching_allocator_alloc(n, dev, st))),
+                        FREE_FN(_guarded_free(torch.cuda.caching_allocator_delete)))
             opt.alloc, opt.free = self._cb
             opt.cuda_stream = st
         elif stream is not None:

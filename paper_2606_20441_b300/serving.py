@@ -13,11 +13,16 @@ split a large fraction of the budget.  A worker's handle (for the mask width of
 its request) has its share as term capacity.  A request starts on whichever worker is free; if it outgrows a small
 share (PP_ERR_CAPACITY) it is re-admitted, with its original arrival time, to
 the queue that only the large workers serve first.  A request that outgrows a
-large share is reported as failed.  With a `route_key` (a workload-class
+large share is reported as failed, unless the server runs exclusive requests:
+then it waits until no other request is queued, the GPU drains (no worker
+takes new work meanwhile), and it runs alone with the whole budget.  Under a
+backlog the exclusive runs thus come after the queued work, with one drain
+instead of one per request.  With a `route_key` (a workload-class
 function), a class that has needed a large share once sends its later requests
-straight to the large workers, so they do not first waste a small worker's
-time.  Keeping the term arrays of a request on
-the device between its layers is the library's ordinary behaviour.
+straight to the large workers, and one that has needed the whole budget
+straight to the exclusive queue, so they do not first waste a smaller share's
+time.  Keeping the term arrays of a request on the device between its layers
+is the library's ordinary behaviour.
 
 The executor is injectable so the scheduling logic can be exercised without a
 GPU.
@@ -98,9 +103,8 @@ class GpuExecutor:
         self.current[worker] = (W, h)
         return h
 
-    def run(self, worker: int, inst: "inputs.Instance"):
+    def _run_on(self, h, inst: "inputs.Instance"):
         try:
-            h = self.handle(worker, inputs.n_words(inst.n_qubits))
             h.load_instance(inst)
             setting = self.tuner.apply(h, inst) if self.tuner is not None else None
             h.run_instance(inst)
@@ -111,6 +115,40 @@ class GpuExecutor:
             return self.pp.PP_OK, e, s.updates, s.n_terms
         except self.pp.PPError as ex:
             return ex.status, None, 0.0, 0
+
+    def run(self, worker: int, inst: "inputs.Instance"):
+        try:
+            h = self.handle(worker, inputs.n_words(inst.n_qubits))
+        except self.pp.PPError as ex:
+            return ex.status, None, 0.0, 0
+        return self._run_on(h, inst)
+
+    def run_exclusive(self, worker: int, inst: "inputs.Instance"):
+        """Runs `inst` alone with the whole budget as its capacity, on
+        `worker`'s stream.  The caller guarantees that no other worker is
+        running: every worker's handle is closed first (its memory goes back
+        to torch's cache, where the exclusive handle finds it), and the
+        exclusive handle is closed afterwards.  An allocation that torch
+        refuses reaches the library as NULL (PP_ERR_NOMEM), never as a bad
+        pointer."""
+        import torch
+        self.close()
+        # hand the released blocks back to the device: the library sizes its
+        # growth from the device's free memory, which torch's cache hides
+        torch.cuda.empty_cache()
+        W = inputs.n_words(inst.n_qubits)
+        per_string = 16 * W + (4 if self.precision == 32 else 8)
+        try:
+            h = self.pp.Handle(64 * W, precision=self.precision,
+                               max_terms=int(sum(self.shares) / (2.6 * per_string)),
+                               torch_memory=True, stream=self.streams[worker].cuda_stream)
+        except self.pp.PPError as ex:
+            return ex.status, None, 0.0, 0
+        self.current[worker] = (W, h)
+        try:
+            return self._run_on(h, inst)
+        finally:
+            self.close()
 
     def cancel(self, worker: int):
         """Stops the propagation running on `worker` (pp_cancel); its run()
@@ -146,26 +184,49 @@ class Server:
     order) or "largest_first" (the largest estimated cost first, ties by
     arrival: under a backlog the longest propagations start first and the short
     ones fill in around them, which shortens the span of a saturated stream;
-    with an empty backlog both take the next arrival)."""
+    with an empty backlog both take the next arrival).  `exclusive` (needs an
+    executor with run_exclusive) re-admits a request that outgrew a large
+    share to an exclusive queue: once no other request is queued, no worker
+    takes new work until every worker is idle, and it runs alone with the
+    whole budget."""
 
     def __init__(self, executor, n_workers: int, n_large: int = 0,
                  clock: Callable[[], float] = time.perf_counter,
-                 route_key: Optional[Callable] = None, backlog: str = "fifo"):
+                 route_key: Optional[Callable] = None, backlog: str = "fifo",
+                 exclusive: bool = False):
         if backlog not in ("fifo", "largest_first"):
             raise ValueError("backlog must be 'fifo' or 'largest_first'")
+        if exclusive and not hasattr(executor, "run_exclusive"):
+            raise ValueError("exclusive requests need an executor with run_exclusive")
         self.backlog = backlog
         self.executor = executor
         self.n_workers = n_workers
         self.n_large = n_large
         self.clock = clock
         self.route_key = route_key
+        self.exclusive = exclusive
         self.large_classes: set = set()
+        self.exclusive_classes: set = set()
         self.outcomes: List[Outcome] = []
 
     def _worker(self, w: int, large: bool):
         while True:
+            alone = False
             with self._cv:
                 while True:
+                    if self._excl_running:
+                        self._cv.wait()
+                        continue
+                    if self._exclusive and not self._fresh and not self._escalated:
+                        # once no other request waits, drain: no new work
+                        # until every worker is idle, then run it alone
+                        if not self._running:
+                            item = self._exclusive.popleft()
+                            alone = True
+                            self._excl_running = True
+                            break
+                        self._cv.wait()
+                        continue
                     if large and self._escalated:
                         item = self._escalated.popleft()
                         break
@@ -184,16 +245,26 @@ class Server:
             start = self.clock()
             with self._cv:
                 self._running[w] = req.rid
-            status, e, upd, terms = self.executor.run(w, req.instance)
+            if alone:
+                status, e, upd, terms = self.executor.run_exclusive(w, req.instance)
+            else:
+                status, e, upd, terms = self.executor.run(w, req.instance)
             done = self.clock()
             with self._cv:
                 self._running.pop(w, None)
+                if alone:
+                    self._excl_running = False
                 if req.rid in self._cancelled:
                     status, e = PP_ERR_TIMEOUT, None
-                if status == PP_ERR_CAPACITY and not large and self.n_large > 0 and req.rid not in self._cancelled:
+                retry = status == PP_ERR_CAPACITY and req.rid not in self._cancelled and not alone
+                if retry and not large and self.n_large > 0:
                     self._escalated.append((req, arrival, True))
                     if self.route_key is not None:
                         self.large_classes.add(self.route_key(req.instance))
+                elif retry and self.exclusive:
+                    self._exclusive.append((req, arrival, True))
+                    if self.route_key is not None:
+                        self.exclusive_classes.add(self.route_key(req.instance))
                 else:
                     self.outcomes.append(Outcome(req.rid, arrival, start, done, w, status, e, upd, terms,
                                                  escalated))
@@ -209,7 +280,7 @@ class Server:
             if any(o.rid == rid for o in self.outcomes):
                 return False
             self._cancelled.add(rid)
-            for q in (self._fresh, self._escalated):
+            for q in (self._fresh, self._escalated, self._exclusive):
                 for item in list(q):
                     if item[0].rid == rid:
                         q.remove(item)
@@ -230,6 +301,8 @@ class Server:
         self._cv = threading.Condition()
         self._fresh: "collections.deque" = collections.deque()
         self._escalated: "collections.deque" = collections.deque()
+        self._exclusive: "collections.deque" = collections.deque()
+        self._excl_running = False
         self._running: dict = {}
         self._cancelled: set = set()
         self._released: set = set()
@@ -255,8 +328,10 @@ class Server:
                     self._pending -= 1
                     self._cv.notify_all()
                     continue
-                if (self.n_large > 0 and self.route_key is not None
-                        and self.route_key(req.instance) in self.large_classes):
+                key = self.route_key(req.instance) if self.route_key is not None else None
+                if self.exclusive and key is not None and key in self.exclusive_classes:
+                    self._exclusive.append((req, max(due, t0), True))
+                elif self.n_large > 0 and key is not None and key in self.large_classes:
                     self._escalated.append((req, max(due, t0), True))
                 else:
                     self._fresh.append((req, max(due, t0), False))

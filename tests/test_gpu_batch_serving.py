@@ -61,6 +61,32 @@ def test_served_results_equal_alone(pp):
         assert o.expect == e_ref
 
 
+def test_requests_too_large_for_every_share_run_alone(pp):
+    """Shares chosen so that the larger requests outgrow both a small and the
+    large share: with exclusive=True they wait for the GPU to drain and run
+    alone with the whole budget (every worker's handle closed first), and the
+    result equals the request run alone, bit for bit."""
+    from paper_2606_20441_b300 import autotune, serving
+    reqs = inputs.workload_serving(count=16, rate_hz=200.0, side_hi=6, steps_hi=10,
+                                   eps_set=(1e-4,), w_max=8)
+    # small shares of ~4.7e6 strings, which the larger requests outgrow by a
+    # wide margin, and a large share smaller still; the whole budget (~3.8e7)
+    # is more than the 2e7 of the reference runs
+    ex = serving.GpuExecutor(n_small=8, hbm_budget_bytes=2e9, precision=32, n_large=1,
+                             large_fraction=0.02)
+    srv = serving.Server(ex, n_workers=8, n_large=1, route_key=autotune.class_key, exclusive=True)
+    try:
+        out = srv.serve(reqs)
+    finally:
+        ex.close()
+    assert all(o.status == pp.PP_OK for o in out), [(o.rid, o.status) for o in out]
+    assert srv.exclusive_classes
+    for o, r in zip(out, sorted(reqs, key=lambda r: r.rid)):
+        e_ref, n_ref = alone(pp, r.instance, 32)
+        assert o.terms == n_ref
+        assert o.expect == e_ref
+
+
 def test_served_fp64_results_against_oracle(pp):
     """A request stream served in FP64 (continuous batching, the autotuner
     varying plans and tile sizes from request to request): every result matches

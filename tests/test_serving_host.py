@@ -50,6 +50,90 @@ def test_failures_are_reported_not_retried():
     assert s["failed"] == 4 and s["served"] == 0
 
 
+def test_requests_that_outgrow_a_large_share_run_alone():
+    """With exclusive=True a request that outgrows a large share waits until
+    every worker is idle (no new work starts meanwhile) and runs alone with the
+    whole budget; its class then goes straight to the exclusive queue."""
+    class Budget(FakeExecutor):
+        def __init__(self, service_s):
+            super().__init__(service_s)
+            self.attempts = {}
+            self.overlap = 0
+
+        def _note(self, inst, kind):
+            self.attempts.setdefault(inst.name, []).append(kind)
+
+        def run(self, worker, inst):
+            self._note(inst, "large" if worker >= 2 else "small")
+            super().run(worker, inst)
+            if inst.n_qubits > 20:
+                return serving.PP_ERR_CAPACITY, None, 0.0, 0
+            return 0, 1.0, 5.0, 1
+
+        def run_exclusive(self, worker, inst):
+            self._note(inst, "alone")
+            with self.lock:
+                self.overlap = max(self.overlap, self.active)
+            super().run(worker, inst)
+            return 0, 2.0, 50.0, 1
+
+    def key(inst):
+        return inst.n_qubits > 20
+
+    reqs = inputs.workload_serving(count=12, rate_hz=800.0, side_hi=6, steps_hi=5)
+    huge = [r for r in reqs if r.instance.n_qubits > 20]
+    assert len(huge) >= 2
+    ex = Budget(0.003)
+    srv = serving.Server(ex, n_workers=2, n_large=1, route_key=key, exclusive=True)
+    out = srv.serve(reqs)
+    assert ex.overlap == 0
+    s = serving.summarize(out)
+    assert s["served"] == 12 and s["failed"] == 0
+    by_rid = {o.rid: o for o in out}
+    for r in huge:
+        assert by_rid[r.rid].escalated and ex.attempts[r.instance.name][-1] == "alone"
+    assert ex.attempts[huge[0].instance.name][0] != "alone"
+    assert srv.exclusive_classes == {True}
+    # the class is known now: later requests of it skip the smaller shares
+    # (a backlog: everything present at once, the ordinary requests released
+    # first), and the exclusive runs wait for the queued work, so every
+    # ordinary request starts before the first exclusive run
+    ex.attempts.clear()
+    backlog = sorted(reqs, key=lambda r: r.instance.n_qubits > 20)
+    again = [inputs.Request(100 + k, 0.0, r.instance) for k, r in enumerate(backlog)]
+    size = {100 + k: r.instance.n_qubits for k, r in enumerate(backlog)}
+    out2 = srv.serve(again)
+    assert all(o.status == 0 for o in out2)
+    for r in huge:
+        assert ex.attempts[r.instance.name] == ["alone"]
+    assert ex.overlap == 0
+    first_alone = min(o.start_s for o in out2 if size[o.rid] > 20)
+    assert all(o.start_s <= first_alone for o in out2 if size[o.rid] <= 20)
+    # without exclusive the same requests fail on the large worker
+    out3 = serving.Server(Budget(0.001), n_workers=2, n_large=1).serve(reqs)
+    assert sum(o.status != 0 for o in out3) == len(huge)
+
+
+def test_exclusive_failures_are_reported():
+    class Never(FakeExecutor):
+        def run(self, worker, inst):
+            super().run(worker, inst)
+            return serving.PP_ERR_CAPACITY, None, 0.0, 0
+
+        def run_exclusive(self, worker, inst):
+            super().run(worker, inst)
+            return serving.PP_ERR_CAPACITY, None, 0.0, 0
+    reqs = inputs.workload_serving(count=3, rate_hz=1000.0, side_hi=4, steps_hi=4)
+    out = serving.Server(Never(0.001), n_workers=1, n_large=1, exclusive=True).serve(reqs)
+    assert [o.status for o in out] == [serving.PP_ERR_CAPACITY] * 3
+    try:
+        serving.Server(FakeExecutor(), n_workers=1, exclusive=True)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("exclusive needs run_exclusive")
+
+
 def test_capacity_failures_escalate_to_large_workers():
     """A request that outgrows a small worker's share is re-admitted to the
     large workers with its original arrival time and served there."""
