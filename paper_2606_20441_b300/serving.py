@@ -85,6 +85,9 @@ class GpuExecutor:
         self.shares += [hbm_budget_bytes * large_fraction / n_large] * n_large
         self.streams = [torch.cuda.Stream() for _ in self.shares]
         self.current: List[Optional[tuple]] = [None] * len(self.shares)   # (W, Handle)
+        self.exclusive: Optional[tuple] = None     # (W, Handle) of the last exclusive run
+        self._excl_worker: Optional[int] = None    # worker driving an exclusive run
+        self._lock = threading.Lock()
 
     def capacity(self, worker: int, W: int) -> int:
         # two term arenas, two overflow areas of a quarter arena and per-bucket
@@ -92,7 +95,19 @@ class GpuExecutor:
         per_string = 16 * W + (4 if self.precision == 32 else 8)
         return int(self.shares[worker] / (2.6 * per_string))
 
+    def _release_exclusive(self):
+        """Closes the exclusive handle kept from the last exclusive run (its
+        memory goes back to the device for the workers' shares)."""
+        import torch
+        with self._lock:
+            if self.exclusive is not None:
+                self.exclusive[1].close()
+                self.exclusive = None
+                torch.cuda.empty_cache()
+
     def handle(self, worker: int, W: int):
+        if self.exclusive is not None:
+            self._release_exclusive()
         cur = self.current[worker]
         if cur is not None and cur[0] == W:
             return cur[1]
@@ -103,10 +118,10 @@ class GpuExecutor:
         self.current[worker] = (W, h)
         return h
 
-    def _run_on(self, h, inst: "inputs.Instance"):
+    def _run_on(self, h, inst: "inputs.Instance", tune: bool = True):
         try:
             h.load_instance(inst)
-            setting = self.tuner.apply(h, inst) if self.tuner is not None else None
+            setting = self.tuner.apply(h, inst) if (tune and self.tuner is not None) else None
             h.run_instance(inst)
             e = h.pp_expect()
             s = h.pp_get_stats()
@@ -125,43 +140,56 @@ class GpuExecutor:
 
     def run_exclusive(self, worker: int, inst: "inputs.Instance"):
         """Runs `inst` alone with the whole budget as its capacity, on
-        `worker`'s stream.  The caller guarantees that no other worker is
-        running: every worker's handle is closed first (its memory goes back
-        to torch's cache, where the exclusive handle finds it), and the
-        exclusive handle is closed afterwards.  An allocation that torch
-        refuses reaches the library as NULL (PP_ERR_NOMEM), never as a bad
-        pointer."""
+        `worker`'s stream, with the library's default plan (no tuning trials
+        on the largest requests).  The caller guarantees that no other worker
+        is running.  The first exclusive run closes every worker's handle
+        (their memory goes back to the device) and opens an exclusive handle;
+        it stays open, at its grown capacity, for the exclusive runs that
+        follow, and is closed when a worker next needs its own handle.  An
+        allocation that torch refuses reaches the library as NULL
+        (PP_ERR_NOMEM), never as a bad pointer."""
         import torch
-        self.close()
-        # hand the released blocks back to the device: the library sizes its
-        # growth from the device's free memory, which torch's cache hides
-        torch.cuda.empty_cache()
         W = inputs.n_words(inst.n_qubits)
-        per_string = 16 * W + (4 if self.precision == 32 else 8)
+        if self.exclusive is None or self.exclusive[0] != W:
+            self._release_exclusive()
+            self._close_workers()
+            # hand the released blocks back to the device: the library sizes its
+            # growth from the device's free memory, which torch's cache hides
+            torch.cuda.empty_cache()
+            per_string = 16 * W + (4 if self.precision == 32 else 8)
+            try:
+                h = self.pp.Handle(64 * W, precision=self.precision,
+                                   max_terms=int(sum(self.shares) / (2.6 * per_string)),
+                                   torch_memory=True, stream=self.streams[worker].cuda_stream)
+            except self.pp.PPError as ex:
+                return ex.status, None, 0.0, 0
+            self.exclusive = (W, h)
+        h = self.exclusive[1]
+        self._excl_worker = worker
         try:
-            h = self.pp.Handle(64 * W, precision=self.precision,
-                               max_terms=int(sum(self.shares) / (2.6 * per_string)),
-                               torch_memory=True, stream=self.streams[worker].cuda_stream)
-        except self.pp.PPError as ex:
-            return ex.status, None, 0.0, 0
-        self.current[worker] = (W, h)
-        try:
-            return self._run_on(h, inst)
+            return self._run_on(h, inst, tune=False)
         finally:
-            self.close()
+            self._excl_worker = None
 
     def cancel(self, worker: int):
         """Stops the propagation running on `worker` (pp_cancel); its run()
         returns PP_ERR_TIMEOUT after the sub-layer in flight."""
         cur = self.current[worker]
+        if self._excl_worker == worker and self.exclusive is not None:
+            cur = self.exclusive
         if cur is not None:
             cur[1].pp_cancel()
 
-    def close(self):
+    def _close_workers(self):
         for k, cur in enumerate(self.current):
             if cur is not None:
                 cur[1].close()
             self.current[k] = None
+
+    def close(self):
+        """Closes every handle, the workers' and the exclusive one."""
+        self._close_workers()
+        self._release_exclusive()
 
 
 def estimated_cost(inst: "inputs.Instance") -> float:
