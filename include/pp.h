@@ -110,7 +110,11 @@ pp_status pp_load_circuit(pp_handle* h, size_t n_gates, const uint64_t* rx, cons
  *   mode     PP_NOISE_INVERSE: coefficients scale by exp(+2 sum lambda) (antinoise);
  *            PP_NOISE_FORWARD: by exp(-2 sum lambda) (the physical channel)
  * The sum of the map's rates must be below 60 (below 40 on an FP32 handle, so
- * that every factor stays within float range), else PP_ERR_ARG.
+ * that every factor stays within float range), and its tables must fit one
+ * CTA's shared memory: 16 KB, plus 2 KB per group of 4 sites, plus 128 B per
+ * 2-site generator support whose sites lie in different groups, plus 4n + 8W B
+ * per distinct distance between the two sites of such supports (a lattice's
+ * nearest-neighbour pairs take a few KB), else PP_ERR_ARG.
  * Generators of weight 1 and 2 are evaluated from tables over groups of four
  * sites plus per-pair corrections (exact fixed-point sums, units of 2^-56); heavier
  * ones from a generic list.  The FP64 form multiplies by the factor in FP64; the

@@ -2030,6 +2030,15 @@ pp_status pp_load_noise(pp_handle* h, int layer, size_t n_gen, const uint64_t* e
         nh.pidx[(size_t)c * n + a] = (int32_t)(nh.c2.size() / 16);
         nh.c2.insert(nh.c2.end(), corr.begin() + 16 * i, corr.begin() + 16 * (i + 1));
     }
+    {
+        // the streaming pass stages every table in one CTA's shared memory
+        const size_t need = noise_smem_layout(n, ng, (int)nh.shift.size(), (int)(nh.c2.size() / 16), W).bytes;
+        if (need > h->smem_optin)
+            return fail(h, PP_ERR_ARG,
+                        "noise map on layer %d: its tables need %zu bytes of shared memory (device: %zu); "
+                        "%zu of its generator pairs cross 4-site groups",
+                        layer, need, h->smem_optin, nh.c2.size() / 16);
+    }
     h->noise.erase(layer);
     // factor tables: entry (i, b) = exp(+-2 * b * 2^(8i - 56)), evaluated in extended
     // precision and rounded once to double, and as a float (head, tail) pair: the

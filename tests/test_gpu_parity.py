@@ -231,6 +231,37 @@ def test_noise_rate_limits_and_largest_factors(pp, precision, layer):
     h.close()
 
 
+def test_noise_tables_must_fit_shared_memory(pp):
+    """The streaming noise pass stages a map's tables in one CTA's shared
+    memory; a map whose 2-site generators cross 4-site groups in thousands of
+    places (every ZZ pair among 80 of 128 qubits) is refused at load time with
+    PP_ERR_ARG, and the handle keeps working (its nearest-neighbour subset
+    loads and propagates)."""
+    n, W = 128, 2
+    h = pp.Handle(n)
+    gx = np.zeros((1, W), np.uint64)
+    gx[0, 0] = np.uint64(1)
+    h.pp_load_circuit(gx, np.zeros((1, W), np.uint64), np.array([0.3]), np.array([0], np.int32), 1)
+    pairs = [(a, b) for a in range(80) for b in range(a + 1, 80)]
+    ex = np.zeros((len(pairs), W), np.uint64)
+    ez = np.zeros((len(pairs), W), np.uint64)
+    for k, (a, b) in enumerate(pairs):
+        ez[k, a // 64] |= np.uint64(1 << (a % 64))
+        ez[k, b // 64] |= np.uint64(1 << (b % 64))
+    lam = np.full(len(pairs), 1e-5)
+    with pytest.raises(pp.PPError) as err:
+        h.pp_load_noise(0, ex, ez, lam)
+    assert err.value.status == pp.PP_ERR_ARG and "shared memory" in str(err.value)
+    near = [k for k, (a, b) in enumerate(pairs) if b == a + 1]
+    h.pp_load_noise(0, ex[near], ez[near], lam[near])
+    ox = np.zeros((1, W), np.uint64)
+    ox[0, 0] = np.uint64(1)   # X on qubit 0: anticommutes with Z0Z1 only
+    h.pp_propagate(ox, np.zeros((1, W), np.uint64), np.array([1.0]), 0.0, -1)
+    x, z, c = h.pp_export_terms()
+    assert len(c) == 1 and abs(c[0] - math.exp(2e-5)) <= 1e-13
+    h.close()
+
+
 # ----------------------------------------------------------------- every processing tier
 
 TIER_CASES = {"6x6_s3": lambda: inputs.workload_6x6(steps=3, eps=1e-5),
