@@ -9,6 +9,7 @@ library's statistics.  This is the program the kernel profiles are taken on.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import sys
 
@@ -41,10 +42,13 @@ def main(argv=None) -> int:
     r.add_argument("--first-tier", type=int, default=0, help="pp_set_tuning first_tier (0: default)")
     r.add_argument("--orbit-tiles", action="store_true", help="pp_set_tuning orbit_tiles: orbit tiles in tier 0")
     r.add_argument("--tile-caps", default="0,0,0,0", help="pp_set_tuning tile_cap of tiers 0-3 (0: default)")
+    r.add_argument("--top-k", type=int, default=0, help="keep the K largest terms after every layer (0: off)")
     a = ap.parse_args(argv)
 
     from . import pp
     inst = _instance(a.workload, a.eps, a.steps, a.w_max)
+    if a.top_k > 0:
+        inst = dataclasses.replace(inst, top_k=a.top_k)
     h = pp.Handle(inst.n_qubits, precision=a.precision, max_terms=a.max_terms, timing=True)
     h.load_instance(inst)
     h.pp_set_tuning(a.fused_gates, a.headroom, a.first_tier, int(a.orbit_tiles),
