@@ -23,7 +23,11 @@ def _instance(name: str, eps: float, steps: int, w_max: int) -> "inputs.Instance
         return inputs.workload_6x6(steps=steps or 10, eps=eps)
     if name == "tfim3x3":
         return inputs.workload_3x3(steps=steps or 4)
-    raise SystemExit("unknown workload %r (tfim7x8, tfim6x6, tfim3x3)" % name)
+    if name == "heavyhex":
+        return inputs.workload_heavy_hex_mirror(steps=steps or 4, eps=eps, w_max=w_max)
+    if name == "mirror3x3":
+        return inputs.workload_trotter2_mirror_3x3(steps=steps or 2, eps=eps)
+    raise SystemExit("unknown workload %r (tfim7x8, tfim6x6, tfim3x3, heavyhex, mirror3x3)" % name)
 
 
 def main(argv=None) -> int:
